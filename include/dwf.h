@@ -1,0 +1,131 @@
+/*
+ * dwf.h -- C ABI of the GB300 (sm_103a) domain-wall fermion library.
+ *
+ * Paper: H. Yin and R. D. Mawhinney, "Improving DWF Simulations: the Force
+ * Gradient Integrator and the Moebius Accelerated DWF Solver", Lattice 2011.
+ *
+ * Operator (Sec. 4, Eq. dirac_eq names D_DW(m); its form is the standard one):
+ *   D(m) = D_W (b + c Q(m)) + 1 - Q(m)            (Shamir: b = 1, c = 0)
+ *   D_W  = (4 - M5) - 1/2 sum_mu [ (1 - g_mu) U_mu(n) d_{n+mu} + (1 + g_mu) U_mu(n-mu)^+ d_{n-mu} ]
+ *   Q(m) psi_s = P- psi_{s+1} + P+ psi_{s-1},  psi_{Ls} := -m psi_0,  psi_{-1} := -m psi_{Ls-1}
+ * with hermitian Euclidean gamma matrices in the chiral basis,
+ * gamma5 = g1 g2 g3 g4 = diag(1,1,-1,-1), P+- = (1 +- gamma5)/2:
+ *   g_k = [[0, -i sigma_k], [i sigma_k, 0]] (k = x,y,z),  g_t = [[0, 1], [1, 0]].
+ *
+ * Boundary layouts (all complex numbers are interleaved re, im; C order):
+ *   gauge field : complex128 [4][T][Z][Y][X][3][3]    (mu = x, y, z, t; U[a][b] row-major)
+ *   5D spinor   : complex128 [Ls][T][Z][Y][X][4][3]   (spin, colour)
+ *   su(3) field : float64    [4][T][Z][Y][X][8]       (components X^j on T_j = i lambda_j / 2)
+ * The lattice site parity is (x + y + z + t) mod 2; "even" is parity 0.
+ *
+ * Ownership: every field pointer is a DEVICE pointer owned by the caller and
+ * must stay valid for the duration of the call.  The library owns only the
+ * lattice handle, its internal (packed) copies of the gauge field and its
+ * workspace, all released by dwf_destroy_lattice.  Work is issued on the
+ * stream given at creation; calls return after the stream has finished the
+ * call's work unless stated otherwise.
+ *
+ * Errors: every call returns a dwf_status and never aborts.  The text of the
+ * last error on a handle is returned by dwf_last_error(handle);
+ * dwf_last_error(NULL) gives the last error of a call that had no valid
+ * handle (for example a failed dwf_create_lattice).
+ */
+#ifndef DWF_H
+#define DWF_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DWF_OK = 0,
+  DWF_ERR_INVALID_ARG = 1,   /* bad pointer, size, parameter or precision */
+  DWF_ERR_CUDA = 2,          /* a CUDA runtime call failed; text has the CUDA error */
+  DWF_ERR_OOM = 3,           /* the library could not allocate its workspace */
+  DWF_ERR_NOT_CONVERGED = 4, /* solver hit max_iter; stats and x hold the last iterate */
+  DWF_ERR_NAN = 5,           /* a NaN or Inf appeared in a solver norm */
+  DWF_ERR_TIMEOUT = 6        /* a bounded device wait gave up */
+} dwf_status;
+
+typedef enum { DWF_F64 = 0, DWF_F32 = 1, DWF_F16 = 2 } dwf_prec;
+
+typedef struct {
+  int dims[4];  /* X, Y, Z, T: each even and >= 2 */
+  int Ls;       /* fifth-dimension extent, 1 <= Ls <= 64 */
+  double M5;    /* domain-wall height (1.8 in all of the paper's setups) */
+  double b, c;  /* Moebius parameters; Shamir DWF is b = 1, c = 0 */
+  int bc_t;     /* +1 periodic or -1 antiperiodic in t (x, y, z are periodic) */
+} dwf_params;
+
+typedef struct dwf_lattice* dwf_lattice_t;
+
+/* Create a lattice handle.  `stream` is a cudaStream_t (NULL = legacy default
+ * stream) on which all of the handle's work is issued.  Sec. 4 (D_DW at Ls,
+ * D'_DW at Ls' are two handles on the same gauge field). */
+dwf_status dwf_create_lattice(const dwf_params* params, void* stream, dwf_lattice_t* out);
+dwf_status dwf_destroy_lattice(dwf_lattice_t h);
+const char* dwf_last_error(dwf_lattice_t h);
+
+/* Upload the gauge field (device complex128 boundary layout).  The library
+ * keeps packed FP64/FP32/FP16 copies with the t boundary phase folded in. */
+dwf_status dwf_set_gauge(dwf_lattice_t h, const void* U);
+
+/* Full 5D operator on whole-lattice spinors (Sec. 4, Eq. dirac_eq):
+ * out = D(m) in, D(m)^+ in, D(m)^+ D(m) in.  `in` and `out` must not alias. */
+dwf_status dwf_apply_M(dwf_lattice_t h, double m, const void* in, void* out);
+dwf_status dwf_apply_Mdag(dwf_lattice_t h, double m, const void* in, void* out);
+dwf_status dwf_apply_MdagM(dwf_lattice_t h, double m, const void* in, void* out);
+
+/* Even-odd Schur operator on even sites: M_pc = A - M_eo A^-1 M_oe with
+ * A = (4-M5)(b+cQ) + 1 - Q and M_eo = -1/2 D_hop^{eo} (b+cQ); dag != 0 gives
+ * M_pc^+.  Whole-lattice boundary layout: odd sites of `in` are ignored, odd
+ * sites of `out` are set to zero. */
+dwf_status dwf_apply_Mpc(dwf_lattice_t h, double m, int dag, const void* in, void* out);
+
+/* Solver controls and statistics. */
+typedef struct {
+  double tol;            /* target |b - D(m) x| / |b| (full, unpreconditioned system) */
+  int max_iter;          /* iteration cap over all inner iterations */
+  dwf_prec inner;        /* DWF_F64: plain FP64 CG; DWF_F32/F16: mixed with FP64 reliable updates */
+  double delta;          /* reliable-update trigger: |r| < delta * max|r| since the last update */
+  int check_every;       /* iterations between host convergence polls (>= 1) */
+} dwf_cg_params;
+
+typedef struct {
+  int iters;             /* CG iterations (each applies M_pc and M_pc^+ once) */
+  int reliable_updates;  /* FP64 residual recomputations */
+  long long hop_calls;   /* 4D Wilson hop applications, each over all Ls slices */
+  long long op_count;    /* the paper's "Op. count" (Table 1): CG iterations x Ls, summed over solves */
+  double true_resid;     /* |b - D(m) x| / |b| in FP64 at exit */
+  double seconds;        /* wall time of the call */
+  long long launches;    /* CUDA kernels the call launched */
+} dwf_stats;
+
+/* Solve D(m) x = b (Sec. 4, Eq. dirac_eq) by even-odd CG on the normal
+ * equations of M_pc.  `x` holds the initial guess on entry (zeros for a cold
+ * start) and the solution on exit.  Returns DWF_ERR_NOT_CONVERGED with the
+ * best iterate if max_iter is reached, DWF_ERR_NAN on a non-finite norm. */
+dwf_status dwf_cg(dwf_lattice_t h, double m, const void* b, void* x,
+                  const dwf_cg_params* params, dwf_stats* stats);
+
+/* Instrumentation (no counterpart in the paper; used to measure the Wilson
+ * hop kernels against the HBM roofline).  With timing enabled every hop
+ * launch on the handle's stream is bracketed by CUDA events.
+ * dwf_set_kernel_timing(h, 1) enables and resets the accumulators, 0 disables.
+ * dwf_get_kernel_time synchronises the stream and returns, for the hop
+ * kernels of precision `prec` since the last reset, the summed device time
+ * in milliseconds, the number of launches and the summed algorithmic bytes
+ * (spinors read and written once, links read once per 4D site).
+ * dwf_get_launch_count returns the number of kernels the handle has
+ * launched since it was created. */
+dwf_status dwf_set_kernel_timing(dwf_lattice_t h, int enable);
+dwf_status dwf_get_kernel_time(dwf_lattice_t h, dwf_prec prec, double* ms, long long* launches, double* bytes);
+dwf_status dwf_get_launch_count(dwf_lattice_t h, long long* launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DWF_H */

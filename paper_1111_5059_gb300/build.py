@@ -1,0 +1,92 @@
+"""Build ``libdwf.so`` in-tree from ``csrc/*.cu`` for sm_103a (GB300).
+
+Each translation unit is compiled by nvcc in parallel into ``_build/`` and
+linked into ``paper_1111_5059_gb300/libdwf.so`` against the shared CUDA
+runtime.  Only nvcc and the host C++ compiler are needed; no GPU.
+"""
+from __future__ import annotations
+
+import glob
+import hashlib
+import os
+import shutil
+import subprocess
+import sys
+from concurrent.futures import ThreadPoolExecutor
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(HERE, "csrc")
+BUILD = os.path.join(HERE, "_build")
+LIB = os.path.join(HERE, "libdwf.so")
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
+              "-Xcompiler", "-Wall", "--expt-relaxed-constexpr"]
+
+
+def nvcc() -> str:
+    for cand in (os.environ.get("NVCC"), shutil.which("nvcc"), "/usr/local/cuda/bin/nvcc"):
+        if cand and os.path.exists(cand):
+            return cand
+    raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libdwf.so")
+
+
+def _sources():
+    return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+
+
+def _headers():
+    return sorted(glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(HERE, "..", "include", "*.h")))
+
+
+def _stamp(src: str, extra: list) -> str:
+    h = hashlib.sha256()
+    for p in [src] + _headers():
+        with open(p, "rb") as f:
+            h.update(f.read())
+    h.update(" ".join(NVCC_FLAGS + ARCH + extra).encode())
+    return h.hexdigest()[:16]
+
+
+def build(verbose: bool = False, ptxas_info: bool = False, extra_flags=None) -> str:
+    """Compile every CUDA source and link libdwf.so; returns the library path."""
+    os.makedirs(BUILD, exist_ok=True)
+    extra = list(extra_flags or [])
+    if ptxas_info:
+        extra += ["-Xptxas", "-v"]
+    cc = nvcc()
+    srcs = _sources()
+    objs = []
+
+    def compile_one(src):
+        base = os.path.splitext(os.path.basename(src))[0]
+        stamp = _stamp(src, extra)
+        obj = os.path.join(BUILD, f"{base}.{stamp}.o")
+        if os.path.exists(obj) and not ptxas_info:
+            return obj, ""
+        cmd = [cc] + ARCH + NVCC_FLAGS + extra + ["-c", src, "-o", obj]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
+        return obj, r.stdout + r.stderr
+
+    with ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 1))) as ex:
+        for obj, log in ex.map(compile_one, srcs):
+            objs.append(obj)
+            if (verbose or ptxas_info) and log:
+                print(log, file=sys.stderr)
+    tmp = LIB + ".tmp"
+    cmd = [cc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, LIB)
+    # drop stale objects of older source versions
+    keep = set(objs)
+    for o in glob.glob(os.path.join(BUILD, "*.o")):
+        if o not in keep:
+            os.remove(o)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(verbose=True, ptxas_info="-v" in sys.argv))

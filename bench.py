@@ -1,19 +1,22 @@
 #!/usr/bin/env python3
 """Benchmark of the domain-wall hot path on GB300.
 
-Metric: DWF solve time to a 1e-10 true residual (MADWF + mixed precision, or
-mixed-precision CG), with plain FP64 CG on the same GPU as the comparison and
-the Wilson hop (Dslash) kernel's achieved HBM bandwidth against the measured
-copy peak.
+Metric: DWF solve time to a 1e-10 true residual |b - D(m) x| / |b|.  The
+headline workload is the Moebius-accelerated solve (MADWF, FP32 inner solves
+with FP64 reliable updates and FP64 defect correction) of Shamir DWF on
+24^3 x 64 x Ls=32 through a Moebius operator at Ls'=12; plain FP64 CG on the
+same GPU and input is measured beside it, and the Wilson hop (Dslash) kernel's
+achieved HBM bandwidth is reported against the measured copy peak.
 
-A step is one solve of D(m) x = b from a zero guess on seeded synthetic
-inputs already resident in HBM.  Defaults finish in a few minutes.
+A step is one solve from a zero guess on seeded synthetic inputs already
+resident in HBM (timed with CUDA events on the solve's stream).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload mixed|madwf]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload madwf|mixed]
                   [--impl native|reference] [--no-fp64] [--no-cpu-baseline]
 
 Under torchrun (N > 1) every rank solves its own replica (no collective on
-the data path); rank 0 prints the JSON line with the max time over ranks.
+the data path, "replicas only"); rank 0 prints the JSON line with the max
+time over ranks.
 """
 from __future__ import annotations
 
@@ -32,49 +35,52 @@ sys.path.insert(0, ROOT)
 HBM_FALLBACK_GBS = 6800.0
 
 WORKLOADS = {
-    # 16^3 x 32 x Ls=16 Shamir, m_f = 0.01, eps = 0.5: mixed-precision CG vs FP64 CG
-    "mixed": dict(name="shamir-16^3x32-Ls16-mixedCG", dims=(16, 16, 16, 32), Ls=16, M5=1.8, m=0.01,
-                  eps=0.5, seed=2, inner="f32",
-                  # FP64 CG iterations to 1e-10 on this input (GB300, dwf_cg inner=f64); scales the
-                  # per-iteration oracle time of the reference arm and the cpu_baseline
-                  fp64_iters=260),
+    # MADWF: Shamir 24^3 x 64 x Ls=32, m_f = 0.002, eps = 0.6, through Moebius Ls' = 12 with
+    # b - c = 1 and b + c = Ls / Ls' (b = 11/6, c = 5/6); 3 defect-correction passes.
+    "madwf": dict(name="madwf-shamir-24^3x64-Ls32-via-mobius-Ls12", dims=(24, 24, 24, 64), Ls=32, M5=1.8,
+                  m=0.002, eps=0.6, seed=3, inner="f32", madwf=True, inner_Ls=12, b=11 / 6, c=5 / 6, n_dc=3,
+                  tol_pv=1e-8, tol_mob=1e-5, sample_T=2),
+    # 16^3 x 32 x Ls=16 Shamir, m_f = 0.01, eps = 0.5: mixed-precision CG
+    "mixed": dict(name="shamir-16^3x32-Ls16-mixedCG", dims=(16, 16, 16, 32), Ls=16, M5=1.8, m=0.01, eps=0.5,
+                  seed=2, inner="f32", madwf=False, sample_T=4),
 }
+# FP64 CG iterations to 1e-10 on each input (GB300, dwf_cg inner=f64); they scale the
+# per-iteration oracle time of the reference arm when the FP64 solve is not run.
+FP64_ITERS = {"madwf": 1500, "mixed": 250}
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default="mixed", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="madwf", choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--inner", default=None, choices=["f32", "f16"], help="inner precision (default per workload)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 CG comparison solve")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tol", type=float, default=1e-10)
     return ap.parse_args()
 
 
-def measured_peaks():
-    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+def measured_peak():
     try:
-        with open(p) as f:
-            d = json.load(f)
-        return float(d["hbm_gbs"]), "measured"
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
     except Exception:
         return HBM_FALLBACK_GBS, "fallback"
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
 
     FIELDS = ["index", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
               "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
               "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
     def __init__(self, gpu_index: int):
-        self.gpu = gpu_index
-        self.proc = None
-        self.lines = []
+        self.gpu, self.proc, self.lines = gpu_index, None, []
 
     def __enter__(self):
         try:
@@ -82,8 +88,7 @@ class ClockSampler:
                 ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + ",".join(self.FIELDS),
                  "--format=csv,noheader,nounits", "-lms", "200"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.t = threading.Thread(target=self._read, daemon=True)
-            self.t.start()
+            threading.Thread(target=self._read, daemon=True).start()
         except Exception:
             self.proc = None
         return self
@@ -102,7 +107,6 @@ class ClockSampler:
 
     def summary(self):
         sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in self.lines:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
@@ -112,7 +116,7 @@ class ClockSampler:
                 mx.append(float(parts[2]))
             except ValueError:
                 continue
-            for n, v in zip(names, parts[5:9]):
+            for n, v in zip(self.NAMES, parts[5:9]):
                 if v.lower().startswith("active"):
                     reasons.add(n)
         if not sm:
@@ -150,61 +154,71 @@ def max_over_ranks(world, v, device):
     return float(t.item())
 
 
+def metric_name(w):
+    return "DWF solve time @1e-10 (" + ("MADWF+mixed" if w["madwf"] else "mixed-precision CG") + ")"
+
+
+def config_of(w, inner):
+    X, Y, Z, T = w["dims"]
+    c = {"workload": w["name"], "lattice": f"{X}x{Y}x{Z}x{T}", "Ls": w["Ls"], "M5": w["M5"], "m_f": w["m"],
+         "eps": w["eps"], "seed": w["seed"], "tol": 1e-10, "inner": inner,
+         "l2": "inputs larger than L2 (each FP32 half-lattice field > 129 MB) plus a 512 MB write between steps"}
+    if w["madwf"]:
+        c.update({"Ls_inner": w["inner_Ls"], "b_inner": w["b"], "c_inner": w["c"], "n_dc": w["n_dc"],
+                  "tol_pv": w["tol_pv"], "tol_mob": w["tol_mob"]})
+    return c
+
+
 # --------------------------------------------------------------------------- oracle timing
 
 
-def oracle_iteration_seconds(w, n_iter=1):
-    """Seconds per CG iteration of the FP64 oracle (M_pc and M_pc^+ once each) on
-    the full workload lattice, on this host's cores."""
+def oracle_iteration_seconds(w):
+    """Seconds per FP64 oracle CG iteration (M_pc then M_pc^+) on the workload,
+    measured on a t-slab of sample_T timeslices and scaled to the full volume
+    (the oracle's work per site does not depend on the lattice extent)."""
     import numpy as np
 
     from oracle import dwf_oracle as O
     from paper_1111_5059_gb300 import inputs
 
-    U = inputs.gauge_field(w["seed"], w["dims"], w["eps"])
-    b = inputs.gaussian_spinor(w["seed"], w["dims"], w["Ls"])
+    X, Y, Z, T = w["dims"]
+    dims = (X, Y, Z, w["sample_T"])
+    U = inputs.gauge_field(w["seed"], dims, w["eps"])
+    b = inputs.gaussian_spinor(w["seed"], dims, w["Ls"])
     eo = O.EO(U, w["m"], w["M5"], w["Ls"])
     v = b * eo.even
     t0 = time.perf_counter()
-    for _ in range(n_iter):
-        q = eo.Mpc(v)
-        v = eo.Mpc(q, True)
-        v = v / np.sqrt(O.norm2(v))
-    return (time.perf_counter() - t0) / n_iter
+    q = eo.Mpc(v)
+    v = eo.Mpc(q, True)
+    v = v / np.sqrt(O.norm2(v))
+    return (time.perf_counter() - t0) * (T / w["sample_T"])
+
+
+def sample_text(w, iters, per_it):
+    X, Y, Z, T = w["dims"]
+    slab = f"a {X}x{Y}x{Z}x{w['sample_T']} t-slab scaled by {T // w['sample_T']}" if w["sample_T"] < T \
+        else "the full lattice"
+    return (f"one FP64 oracle CG iteration (M_pc then M_pc^+) on {slab} ({per_it:.1f} s per full-volume "
+            f"iteration), times the {iters} iterations of the FP64 CG solve of this input")
 
 
 def run_reference(args, w):
-    world, rank, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
-    if rank != 0:
+    if int(os.environ.get("RANK", "0")) != 0:
         return
     for _ in range(args.warmup):
         oracle_iteration_seconds(w)
     times = [oracle_iteration_seconds(w) for _ in range(args.steps)]
     per_it = statistics.mean(times)
-    value = per_it * w["fp64_iters"]
-    sample = (f"1 oracle CG iteration (M_pc then M_pc^+) on the full {w['name']} lattice per step, "
-              f"scaled by the {w['fp64_iters']} FP64 CG iterations the solve takes")
+    iters = FP64_ITERS[args.workload]
+    value = per_it * iters
     line = {"impl": "reference", "metric": metric_name(w), "value": value, "unit": "s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_it * 1e3,
-            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config_of(w),
-            "cpu_baseline": {"value": value, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample},
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_it * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_of(w, "f64"),
+            "cpu_baseline": {"value": value, "unit": "s", "cores": 1, "kind": "oracle",
+                             "sample": sample_text(w, iters, per_it)},
             "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
-
-
-def metric_name(w):
-    return "DWF solve time @1e-10 (" + ("MADWF+mixed" if w.get("madwf") else "mixed-precision CG") + ")"
-
-
-def config_of(w):
-    X, Y, Z, T = w["dims"]
-    c = {"workload": w["name"], "lattice": f"{X}x{Y}x{Z}x{T}", "Ls": w["Ls"], "M5": w["M5"], "m_f": w["m"],
-         "eps": w["eps"], "seed": w["seed"], "tol": 1e-10, "inner": w["inner"],
-         "l2": "inputs larger than L2 between steps (working set > 129 MB) plus a 512 MB L2 flush write"}
-    if w.get("madwf"):
-        c.update({"Ls_inner": w["inner_Ls"], "b_inner": w["b"], "c_inner": w["c"], "n_dc": w["n_dc"]})
-    return c
 
 
 # --------------------------------------------------------------------------- native arm
@@ -213,10 +227,10 @@ def config_of(w):
 def main():
     args = parse()
     w = WORKLOADS[args.workload]
+    inner = args.inner or w["inner"]
     if args.impl == "reference":
         run_reference(args, w)
         return
-    import numpy as np
     import torch
 
     world, rank, local = dist_init()
@@ -228,7 +242,7 @@ def main():
         from paper_1111_5059_gb300 import build
 
         build.build()
-    hbm_peak, peak_src = measured_peaks()
+    hbm_peak, peak_src = measured_peak()
 
     U = torch.from_numpy(inputs.gauge_field(w["seed"], w["dims"], w["eps"])).to(dev)
     b_host = torch.from_numpy(inputs.gaussian_spinor(w["seed"], w["dims"], w["Ls"])).pin_memory()
@@ -237,19 +251,28 @@ def main():
     stream = torch.cuda.current_stream(dev)
     lat = dwf.Lattice(w["dims"], w["Ls"], w["M5"], 1.0, 0.0, 1, stream=stream, device=dev)
     lat.set_gauge(U)
+    lats = [lat]
+    if w["madwf"]:
+        mob = dwf.Lattice(w["dims"], w["inner_Ls"], w["M5"], w["b"], w["c"], 1, stream=stream, device=dev)
+        mob.set_gauge(U)
+        lats.append(mob)
+    del U
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def solve(bb):
-        return lat.cg(w["m"], bb, tol=args.tol, inner=w["inner"], delta=0.1, check_every=10)
+        if w["madwf"]:
+            return dwf.madwf_solve(lat, mob, w["m"], bb, n_dc=w["n_dc"], tol_pv=w["tol_pv"], tol_mob=w["tol_mob"],
+                                   tol_final=args.tol, inner_prec=inner, delta=0.1, check_every=10)
+        return lat.cg(w["m"], bb, tol=args.tol, inner=inner, delta=0.1, check_every=10)
 
     for _ in range(args.warmup):
         r = solve(b)
     torch.cuda.synchronize()
 
-    # ---- timed region: K solves, inputs resident in HBM
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    lat.set_kernel_timing(True)
-    n0 = lat.launch_count()
+    # ---- timed region: K solves with inputs resident in HBM
+    for L in lats:
+        L.set_kernel_timing(True)
+    n0 = sum(L.launch_count() for L in lats)
     step_ms, stats = [], []
     barrier(world)
     torch.cuda.synchronize()
@@ -265,19 +288,20 @@ def main():
             stats.append(r.stats)
     torch.cuda.synchronize()
     barrier(world)
-    launches = lat.launch_count() - n0
-    kt = lat.kernel_time(w["inner"])
-    lat.set_kernel_timing(False)
+    launches = sum(L.launch_count() for L in lats) - n0
+    kts = [L.kernel_time(inner) for L in lats]
+    for L in lats:
+        L.set_kernel_timing(False)
+    kt = {k: sum(d[k] for d in kts) for k in ("ms", "launches", "bytes")}
     total_ms = max_over_ranks(world, sum(step_ms), dev)
     ms_step = total_ms / args.steps
-    value = ms_step / 1e3 / world  # seconds per solve, whole job (replicas solve concurrently)
+    value = ms_step / 1e3 / world  # seconds per solve for the whole job
+    st = stats[-1]
+    true_res = st["total"]["true_resid"] if w["madwf"] else st["true_resid"]
 
-    x = r.x.cpu().numpy()
-    true_res = r.stats["true_resid"]
-
-    # ---- e2e through the C ABI with host buffers
-    e2e_ms = []
-    for _ in range(max(1, min(args.steps, 3))):
+    # ---- e2e: the same solve through the C ABI from pinned host buffers
+    e2e = []
+    for _ in range(max(1, min(args.steps, 2))):
         flush.fill_(1.0)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -286,52 +310,61 @@ def main():
         x_host.copy_(rr.x, non_blocking=True)
         e1.record(stream)
         e1.synchronize()
-        e2e_ms.append(e0.elapsed_time(e1))
-    e2e_ms = max_over_ranks(world, statistics.mean(e2e_ms), dev)
+        e2e.append(e0.elapsed_time(e1))
+        del bd, rr
+    e2e_ms = max_over_ranks(world, statistics.mean(e2e), dev)
 
-    # ---- FP64 CG comparison on the same GPU
-    fp64 = None
+    # ---- comparisons on the same GPU: plain FP64 CG (and mixed CG for MADWF)
+    comp = {}
     if not args.no_fp64:
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        rf = lat.cg(w["m"], b, tol=args.tol, inner="f64", check_every=10)
-        torch.cuda.synchronize()
-        fp64 = {"seconds": time.perf_counter() - t0, "iters": rf.stats["iters"], "op_count": rf.stats["op_count"],
-                "true_resid": rf.stats["true_resid"]}
-        fp64["speedup_of_headline"] = fp64["seconds"] / (ms_step / 1e3)
+        for name, prec in (("fp64_cg", "f64"),) + ((("mixed_cg", inner),) if w["madwf"] else ()):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rf = lat.cg(w["m"], b, tol=args.tol, inner=prec, check_every=10)
+            e1.record(stream)
+            e1.synchronize()
+            secs = e0.elapsed_time(e1) / 1e3
+            comp[name] = {"seconds": secs, "iters": rf.stats["iters"], "op_count": rf.stats["op_count"],
+                          "true_resid": rf.stats["true_resid"], "speedup_of_headline": secs / (ms_step / 1e3)}
+            del rf
 
     achieved = kt["bytes"] / (kt["ms"] / 1e3) / 1e9 if kt["ms"] > 0 else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
             "frac": (achieved / hbm_peak) if achieved else None, "traffic": None,
-            "kernel": f"hop_kernel<{w['inner']}> (Wilson hop x Ls with fused s-local epilogues)",
+            "kernel": f"hop_kernel<{inner}> (Wilson hop at every s with fused fifth-dimension epilogues)",
             "launches": kt["launches"], "avg_launch_us": kt["ms"] / max(1, kt["launches"]) * 1e3,
             "bytes_per_launch": kt["bytes"] / max(1, kt["launches"]),
-            "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)" if peak_src == "measured" else "fallback"}
-
+            "share_of_step": kt["ms"] / max(1e-9, sum(step_ms)),
+            "peak_source": ("of measured hbm_gbs (MEASURED_PEAKS.json)" if peak_src == "measured"
+                            else "of fallback 6.8 TB/s")}
+    if w["madwf"]:
+        solve_info = {"passes": st["passes"], "pass_resid": st["pass_resid"], "true_resid": true_res,
+                      "mobius_iters": st["mobius"]["iters"], "pv_iters": st["pv"]["iters"],
+                      "final_iters": st["final_cg"]["iters"],
+                      "op_count": {"mobius": st["mobius"]["op_count"], "pv": st["pv"]["op_count"],
+                                   "final": st["final_cg"]["op_count"], "total": st["total"]["op_count"]},
+                      "step_ms": step_ms}
+    else:
+        solve_info = {"iters": st["iters"], "reliable_updates": st["reliable_updates"], "op_count": st["op_count"],
+                      "true_resid": true_res, "step_ms": step_ms}
     line = {"metric": metric_name(w), "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic", "config": config_of(w),
-            "roofline": roof,
+            "vs_baseline": None, "dtype": "f32+f64" if inner == "f32" else "f16-storage/f32+f64",
+            "data": "synthetic", "config": config_of(w, inner), "roofline": roof,
             "e2e": {"value": e2e_ms / 1e3 / world, "unit": "s", "h2d_bytes_per_step": b_host.numel() * 16,
                     "d2h_bytes_per_step": x_host.numel() * 16},
-            "gpu_launches": launches,
-            "solve": {"iters": stats[-1]["iters"], "reliable_updates": stats[-1]["reliable_updates"],
-                      "op_count": stats[-1]["op_count"], "true_resid": true_res,
-                      "step_ms": step_ms},
-            "fp64_cg": fp64}
+            "gpu_launches": launches, "solve": solve_info, "clocks": clk.summary()}
+    line.update(comp)
     if rank == 0:
-        with ClockSampler(local):
-            pass
-        line["clocks"] = clk.summary()
         if not args.no_cpu_baseline:
+            iters = comp["fp64_cg"]["iters"] if "fp64_cg" in comp else FP64_ITERS[args.workload]
             per_it = oracle_iteration_seconds(w)
-            line["cpu_baseline"] = {
-                "value": per_it * w["fp64_iters"], "unit": "s", "cores": 1, "kind": "oracle",
-                "sample": (f"1 FP64 oracle CG iteration (M_pc, M_pc^+) on the full {w['name']} lattice "
-                           f"({per_it:.1f} s), scaled by the {w['fp64_iters']} iterations of the FP64 solve")}
+            line["cpu_baseline"] = {"value": per_it * iters, "unit": "s", "cores": 1, "kind": "oracle",
+                                    "sample": sample_text(w, iters, per_it)}
         print(json.dumps(line), flush=True)
-    del x
-    lat.close()
+    for L in lats:
+        L.close()
     if world > 1:
         import torch.distributed as dist
 

@@ -110,6 +110,98 @@ typedef struct {
 dwf_status dwf_cg(dwf_lattice_t h, double m, const void* b, void* x,
                   const dwf_cg_params* params, dwf_stats* stats);
 
+/* Moebius-accelerated DWF solve (Sec. 4, the four-step algorithm with
+ * Eqs. trans_5d_4d_source, mob_eq_4d, mob_eq_5d and recon; Sec. 5, defect
+ * correction; Table 1).  `outer` is the Shamir lattice (b = 1, c = 0) of
+ * extent Ls on which D_DW(m) x = b is solved; `inner` is a Moebius lattice
+ * with the same 4D extents and gauge field (set on both handles) and extent
+ * Ls' (usually Ls' < Ls).  Each of the n_dc defect-correction passes does two
+ * Pauli-Villars solves D_DW(1) (tolerance tol_pv) and one Moebius solve
+ * D'_DW(m) (tol_mob) on the current residual and adds the reconstructed 5D
+ * guess to x; a final DWF solve to tol_final starts from that guess.  All
+ * solves use CG on the normal equations at the `inner` precision with FP64
+ * reliable updates; residuals and the accumulated solution stay FP64.
+ * `x` need not be initialised; b and x are whole-lattice boundary-layout
+ * device spinors of the outer lattice.  Work runs on the outer handle's
+ * stream.  Returns DWF_ERR_NOT_CONVERGED if the final solve hits max_iter
+ * (an inexact intermediate solve is tolerated and visible in the stats). */
+#define MADWF_MAX_PASSES 16
+typedef struct {
+  int n_dc;            /* defect-correction passes (3 in the paper's Table 1), 0..16 */
+  double tol_pv;       /* relative residual of the Pauli-Villars solves */
+  double tol_mob;      /* relative residual of the Moebius solves */
+  double tol_final;    /* target |b - D(m) x| / |b| of the final DWF solve */
+  dwf_prec inner;      /* precision of the inner CG iterations */
+  int max_iter;        /* iteration cap per solve */
+  double delta;        /* reliable-update trigger of every solve */
+  int check_every;     /* host convergence polls */
+} madwf_params;
+
+typedef struct {
+  dwf_stats total;     /* sums over all solves; total.true_resid is the result's */
+  dwf_stats pv;        /* the 2 n_dc Pauli-Villars solves (op_count in units of Ls) */
+  dwf_stats mobius;    /* the n_dc Moebius solves (op_count in units of Ls') */
+  dwf_stats final_cg;  /* the final warm-started DWF solve */
+  int passes;          /* defect-correction passes done */
+  double pass_resid[MADWF_MAX_PASSES]; /* |b - D x| / |b| after each pass */
+} madwf_stats;
+
+dwf_status madwf_solve(dwf_lattice_t outer, dwf_lattice_t inner, double m, const void* b, void* x,
+                       const madwf_params* params, madwf_stats* stats);
+
+/* Pseudofermion action and fermion force (Sec. 2 and 3).
+ *
+ * A quotient term (m1, m2) is the Hasenbusch factor det(M1^+ M1)/det(M2^+ M2)
+ * of Sec. 3 (m2 = 1: Pauli-Villars denominator), with M = M_pc the even-odd
+ * Schur operator of the lattice; its action is
+ *   S = phi^+ M2 (M1^+ M1)^-1 M2^+ phi = |M1 X|^2,   X = (M1^+ M1)^-1 M2^+ phi.
+ * dwf_force solves for X with CG on the normal equations (parameters `cg`),
+ * and writes, summed over the `nterms` terms:
+ *   S  (host double, may be NULL): the total action;
+ *   F  (device float64 [4][T][Z][Y][X][8], may be NULL): the force components
+ *      F^j(n, mu) = e_j S, the derivative of S along U_mu(n) -> exp(h T_j) U_mu(n),
+ *      T_j = i lambda_j / 2 (Sec. 2: F^j = e^j(S));
+ *   G  (device complex128 [4][T][Z][Y][X][3][3], may be NULL): the complex-
+ *      matrix gradient 2 dS / d conj(U) of S as a function of the boundary-
+ *      layout links (the convention of torch.autograd for complex inputs).
+ * phi[t] are device whole-lattice spinors (only even sites are used).
+ * X_io (may be NULL; entries may be NULL): device whole-lattice spinors that
+ * hold the initial guess for term t's solve on entry and its solution X on
+ * exit (even sites; odd sites set to zero) -- the "force gradient
+ * forecasting" of Sec. 2 passes the first solve's X to the second. */
+typedef struct {
+  double m1, m2;
+} dwf_quotient;
+
+dwf_status dwf_force(dwf_lattice_t h, int nterms, const dwf_quotient* terms, const void* const* phi,
+                     void* const* X_io, void* F, void* G, double* S, const dwf_cg_params* cg, dwf_stats* stats);
+
+/* The force-gradient link update (Sec. 2, Eq. for U'): for every link,
+ * U_out = exp(coeff * sum_j X^j T_j) U_in with X float64 [4][T][Z][Y][X][8]
+ * and U complex128 boundary layout (U_out may equal U_in).  coeff =
+ * -tau^2/24 with X = F gives U' of the force-gradient step; coeff = dt with
+ * X = p is the link (Q) update of the integrator. */
+dwf_status fgi_link_update(dwf_lattice_t h, const void* X, double coeff, const void* U_in, void* U_out);
+
+/* p += coeff * F on float64 [4][T][Z][Y][X][8] su(3) components (the
+ * momentum (P) update). */
+dwf_status dwf_momentum_update(dwf_lattice_t h, const void* F, double coeff, void* p);
+
+/* Kinetic energy 1/2 sum (p^j)^2 (FP64). */
+dwf_status dwf_kinetic(dwf_lattice_t h, const void* p, double* T);
+
+/* One force-gradient PQPQP step (Sec. 2, Eq. 1, with the two-step
+ * implementation of the force-gradient term):
+ *   P(tau/6) Q(tau/2) [F = F(U); U' = exp(-tau^2/24 F^j T_j) U; p -= 2/3 tau F(U')] Q(tau/2) P(tau/6)
+ * U (device complex128 boundary layout) and p (device float64 components)
+ * are updated in place; the handle's gauge field is left set to the new U.
+ * With forecast != 0 the solve of F(U') starts from the solutions of F(U).
+ * stats->iters sums the CG iterations of the five force evaluations;
+ * fg_iters[0] and fg_iters[1] (may be NULL) receive those of F(U) and F(U')
+ * in the force-gradient step. */
+dwf_status fgi_step(dwf_lattice_t h, int nterms, const dwf_quotient* terms, const void* const* phi, void* U, void* p,
+                    double tau, int forecast, const dwf_cg_params* cg, dwf_stats* stats, int* fg_iters);
+
 /* Instrumentation (no counterpart in the paper; used to measure the Wilson
  * hop kernels against the HBM roofline).  With timing enabled every hop
  * launch on the handle's stream is bracketed by CUDA events.

@@ -1,21 +1,22 @@
 // Level-1 vector kernels on one-parity spinor fields and the CG scalar
-// recurrences.  Every kernel walks the (h, s) sites with a grid-stride loop;
-// each thread loads and stores whole 24-real spinors through the storage
-// traits, so FP64, FP32 and FP16 (scaled) fields share one code path.
-// Reductions are deterministic: FP64 per-block partials, then one block sums
-// them in a fixed order.
+// recurrences.
+//
+// All precisions share one element order (see dwf_internal.h), so kernels
+// whose output is FP64 or FP32 stream the fields chunk by chunk (4 reals: the
+// re and im parts of one complex component of a slice pair), whatever the
+// input precisions.  An FP16 output needs the largest component of each slice
+// for its scale, so those kernels walk whole slice pairs (h, j) instead.
+// Reductions are deterministic: per-block partials, then one block sums them
+// in a fixed order.  Per-chunk sums of squares are formed in the data's own
+// precision (FP64 issue rate is low on GB300) and accumulated in FP64.
 #include "dwf_internal.h"
 
 namespace dwf {
 
 namespace {
 
-template <class S> CFieldRef<S> cr(const Field& f) {
-  return CFieldRef<S>{reinterpret_cast<const typename Store<S>::chunk_t*>(f.v), f.norm};
-}
-template <class S> FieldRef<S> wr(const Field& f) {
-  return FieldRef<S>{reinterpret_cast<typename Store<S>::chunk_t*>(f.v), f.norm};
-}
+template <class S> CFieldRef<S> cr(const Field& f) { return CFieldRef<S>{reinterpret_cast<const S*>(f.v), f.norm}; }
+template <class S> FieldRef<S> wr(const Field& f) { return FieldRef<S>{reinterpret_cast<S*>(f.v), f.norm}; }
 
 int grid_for(long n) {
   long b = (n + kBlasThreads - 1) / kBlasThreads;
@@ -23,101 +24,201 @@ int grid_for(long n) {
   return (int)(b < cap ? (b < 1 ? 1 : b) : cap);
 }
 
+// ---- chunk io: chunk q = (h * 12 + k) * Lh + j holds (re s0, re s1, im s0, im s1)
+__device__ __forceinline__ void ld_chunk(CFieldRef<double> f, long q, int, double* v) {
+  const double2* p = reinterpret_cast<const double2*>(f.v) + 2 * q;
+  const double2 a = __ldg(p), b = __ldg(p + 1);
+  v[0] = a.x;
+  v[1] = a.y;
+  v[2] = b.x;
+  v[3] = b.y;
+}
+__device__ __forceinline__ void ld_chunk(CFieldRef<float> f, long q, int, float* v) {
+  const float4 a = __ldg(reinterpret_cast<const float4*>(f.v) + q);
+  v[0] = a.x;
+  v[1] = a.y;
+  v[2] = a.z;
+  v[3] = a.w;
+}
+__device__ __forceinline__ void ld_chunk(CFieldRef<__half> f, long q, int Lh, float* v) {
+  const long j = q % Lh, h = q / ((long)12 * Lh);
+  const float2 sc = __ldg(reinterpret_cast<const float2*>(f.norm) + h * Lh + j);
+  const uint2 a = __ldg(reinterpret_cast<const uint2*>(f.v) + q);
+  const float2 r = __half22float2(*reinterpret_cast<const __half2*>(&a.x));
+  const float2 i = __half22float2(*reinterpret_cast<const __half2*>(&a.y));
+  v[0] = r.x * sc.x;
+  v[1] = r.y * sc.y;
+  v[2] = i.x * sc.x;
+  v[3] = i.y * sc.y;
+}
+__device__ __forceinline__ void st_chunk(FieldRef<double> f, long q, const double* v) {
+  double2* p = reinterpret_cast<double2*>(f.v) + 2 * q;
+  p[0] = make_double2(v[0], v[1]);
+  p[1] = make_double2(v[2], v[3]);
+}
+__device__ __forceinline__ void st_chunk(FieldRef<float> f, long q, const float* v) {
+  reinterpret_cast<float4*>(f.v)[q] = make_float4(v[0], v[1], v[2], v[3]);
+}
+
+// ---- norm
 template <class S>
-__global__ void __launch_bounds__(kBlasThreads) k_norm2(CFieldRef<S> x, long n, int Ls, double* partials) {
+__global__ void __launch_bounds__(kBlasThreads) k_norm2(CFieldRef<S> x, long nq, int Lh, double* partials) {
   __shared__ double red[32];
   typedef typename Store<S>::calc_t C;
   double acc = 0.0;
-  for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) {
-    const long h = q / Ls;
-    const int s = (int)(q - h * Ls);
-    C v[24];
-    load_spinor<S>(x, h, s, Ls, v);
-    C ps = 0;
-#pragma unroll
-    for (int k = 0; k < 24; ++k) ps = fma(v[k], v[k], ps);
-    acc += (double)ps;
+  for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += (long)gridDim.x * blockDim.x) {
+    C v[4];
+    ld_chunk(x, q, Lh, v);
+    acc += (double)(v[0] * v[0] + v[1] * v[1] + v[2] * v[2] + v[3] * v[3]);
   }
   double t = block_sum<kBlasThreads>(acc, red);
   if (threadIdx.x == 0) partials[blockIdx.x] = t;
 }
 
+// ---- y = a x + b y  (y FP64 / FP32)
 template <class SX, class SY>
-__global__ void __launch_bounds__(kBlasThreads) k_axpby(double a, CFieldRef<SX> x, double b, FieldRef<SY> y,
-                                                       long n, int Ls, int read_y) {
-  typedef typename Store<SX>::calc_t CX;
+__global__ void __launch_bounds__(kBlasThreads) k_axpby_c(double a, CFieldRef<SX> x, double b, FieldRef<SY> y,
+                                                         long nq, int Lh, int read_y) {
   typedef typename Store<SY>::calc_t CY;
-  for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) {
-    const long h = q / Ls;
-    const int s = (int)(q - h * Ls);
-    CX xv[24];
-    CY yv[24];
-    if (a != 0.0) load_spinor<SX>(x, h, s, Ls, xv);
-    if (read_y) {
-      load_spinor<SY>(CFieldRef<SY>{y.v, y.norm}, h, s, Ls, yv);
-    }
+  typedef typename Store<SX>::calc_t CX;
+  for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += (long)gridDim.x * blockDim.x) {
+    CX xv[4] = {0, 0, 0, 0};
+    CY yv[4] = {0, 0, 0, 0};
+    if (a != 0.0) ld_chunk(x, q, Lh, xv);
+    if (read_y) ld_chunk(CFieldRef<SY>{y.v, y.norm}, q, Lh, yv);
 #pragma unroll
-    for (int k = 0; k < 24; ++k) {
-      CY r = 0;
-      if (read_y) r = (CY)(b * (double)yv[k]);
-      if (a != 0.0) r += (CY)(a * (double)xv[k]);
-      yv[k] = r;
-    }
-    store_spinor<SY>(y, h, s, Ls, yv);
+    for (int e = 0; e < 4; ++e) yv[e] = (CY)(a * (double)xv[e] + b * (double)yv[e]);
+    st_chunk(y, q, yv);
   }
 }
 
-// x += alpha p;  r -= alpha q;  partial |r|^2.  The solution accumulator x
-// may be stored at a higher precision (SX) than the iterated vectors (S).
+// ---- y = a x + b y  (y FP16: whole slice pairs)
+template <class SX>
+__global__ void __launch_bounds__(kBlasThreads) k_axpby_p(double a, CFieldRef<SX> x, double b, FieldRef<__half> y,
+                                                         long npairs, int Lh, int read_y) {
+  typedef typename Store<SX>::calc_t CX;
+  for (long pi = (long)blockIdx.x * blockDim.x + threadIdx.x; pi < npairs; pi += (long)gridDim.x * blockDim.x) {
+    const long h = pi / Lh;
+    const int j = (int)(pi - h * Lh);
+    float2 re[12], im[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      const long q = (h * 12 + k) * Lh + j;
+      CX xv[4] = {0, 0, 0, 0};
+      float yv[4] = {0, 0, 0, 0};
+      if (a != 0.0) ld_chunk(x, q, Lh, xv);
+      if (read_y) ld_chunk(CFieldRef<__half>{y.v, y.norm}, q, Lh, yv);
+      float o[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) o[e] = (float)(a * (double)xv[e] + b * (double)yv[e]);
+      re[k] = make_float2(o[0], o[1]);
+      im[k] = make_float2(o[2], o[3]);
+    }
+    store_pair(y, h, j, Lh, re, im);
+  }
+}
+
+// ---- x += alpha p; r -= alpha q; partial |r|^2   (x may be stored at a higher precision)
 template <class S, class SX>
-__global__ void __launch_bounds__(kBlasThreads) k_cg_xr(const double* alpha, CFieldRef<S> p, CFieldRef<S> q,
-                                                       FieldRef<SX> x, FieldRef<S> r, long n, int Ls,
-                                                       double* partials) {
+__global__ void __launch_bounds__(kBlasThreads) k_cg_xr_c(const double* alpha, CFieldRef<S> p, CFieldRef<S> q,
+                                                         FieldRef<SX> x, FieldRef<S> r, long nq, int Lh,
+                                                         double* partials) {
   __shared__ double red[32];
   typedef typename Store<S>::calc_t C;
   typedef typename Store<SX>::calc_t CX;
   const C a = (C)(*alpha);
   double acc = 0.0;
-  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-    const long h = i / Ls;
-    const int s = (int)(i - h * Ls);
-    C pv[24], qv[24], rv[24];
-    CX xv[24];
-    load_spinor<S>(p, h, s, Ls, pv);
-    load_spinor<S>(q, h, s, Ls, qv);
-    load_spinor<SX>(CFieldRef<SX>{x.v, x.norm}, h, s, Ls, xv);
-    load_spinor<S>(CFieldRef<S>{r.v, r.norm}, h, s, Ls, rv);
-#pragma unroll
-    for (int k = 0; k < 24; ++k) {
-      xv[k] = fma((CX)a, (CX)pv[k], xv[k]);
-      rv[k] = fma(-a, qv[k], rv[k]);
-    }
-    store_spinor<SX>(x, h, s, Ls, xv);
-    store_spinor<S>(r, h, s, Ls, rv);
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += (long)gridDim.x * blockDim.x) {
+    C pv[4], qv[4], rv[4];
+    CX xv[4];
+    ld_chunk(p, i, Lh, pv);
+    ld_chunk(q, i, Lh, qv);
+    ld_chunk(CFieldRef<SX>{x.v, x.norm}, i, Lh, xv);
+    ld_chunk(CFieldRef<S>{r.v, r.norm}, i, Lh, rv);
     C ps = 0;
 #pragma unroll
-    for (int k = 0; k < 24; ++k) ps = fma(rv[k], rv[k], ps);
+    for (int e = 0; e < 4; ++e) {
+      xv[e] = fma((CX)a, (CX)pv[e], xv[e]);
+      rv[e] = fma(-a, qv[e], rv[e]);
+      ps = fma(rv[e], rv[e], ps);
+    }
+    st_chunk(x, i, xv);
+    st_chunk(r, i, rv);
     acc += (double)ps;
   }
   double t = block_sum<kBlasThreads>(acc, red);
   if (threadIdx.x == 0) partials[blockIdx.x] = t;
 }
 
-// p = s + beta p
+__global__ void __launch_bounds__(kBlasThreads) k_cg_xr_p(const double* alpha, CFieldRef<__half> p,
+                                                         CFieldRef<__half> q, FieldRef<float> x, FieldRef<__half> r,
+                                                         long npairs, int Lh, double* partials) {
+  __shared__ double red[32];
+  const float a = (float)(*alpha);
+  double acc = 0.0;
+  for (long pi = (long)blockIdx.x * blockDim.x + threadIdx.x; pi < npairs; pi += (long)gridDim.x * blockDim.x) {
+    const long h = pi / Lh;
+    const int j = (int)(pi - h * Lh);
+    float2 re[12], im[12];
+    float ps = 0.f;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      const long c = (h * 12 + k) * Lh + j;
+      float pv[4], qv[4], rv[4], xv[4];
+      ld_chunk(p, c, Lh, pv);
+      ld_chunk(q, c, Lh, qv);
+      ld_chunk(CFieldRef<float>{x.v, x.norm}, c, Lh, xv);
+      ld_chunk(CFieldRef<__half>{r.v, r.norm}, c, Lh, rv);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        xv[e] = fmaf(a, pv[e], xv[e]);
+        rv[e] = fmaf(-a, qv[e], rv[e]);
+        ps = fmaf(rv[e], rv[e], ps);
+      }
+      st_chunk(x, c, xv);
+      re[k] = make_float2(rv[0], rv[1]);
+      im[k] = make_float2(rv[2], rv[3]);
+    }
+    store_pair(r, h, j, Lh, re, im);
+    acc += (double)ps;
+  }
+  double t = block_sum<kBlasThreads>(acc, red);
+  if (threadIdx.x == 0) partials[blockIdx.x] = t;
+}
+
+// ---- p = s + beta p
 template <class S>
-__global__ void __launch_bounds__(kBlasThreads) k_cg_p(const double* beta, CFieldRef<S> sv, FieldRef<S> p,
-                                                      long n, int Ls) {
+__global__ void __launch_bounds__(kBlasThreads) k_cg_p_c(const double* beta, CFieldRef<S> sv, FieldRef<S> p, long nq,
+                                                        int Lh) {
   typedef typename Store<S>::calc_t C;
   const C b = (C)(*beta);
-  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-    const long h = i / Ls;
-    const int s = (int)(i - h * Ls);
-    C a[24], c[24];
-    load_spinor<S>(sv, h, s, Ls, a);
-    load_spinor<S>(CFieldRef<S>{p.v, p.norm}, h, s, Ls, c);
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += (long)gridDim.x * blockDim.x) {
+    C a[4], c[4];
+    ld_chunk(sv, i, Lh, a);
+    ld_chunk(CFieldRef<S>{p.v, p.norm}, i, Lh, c);
 #pragma unroll
-    for (int k = 0; k < 24; ++k) c[k] = fma(b, c[k], a[k]);
-    store_spinor<S>(p, h, s, Ls, c);
+    for (int e = 0; e < 4; ++e) c[e] = fma(b, c[e], a[e]);
+    st_chunk(p, i, c);
+  }
+}
+
+__global__ void __launch_bounds__(kBlasThreads) k_cg_p_p(const double* beta, CFieldRef<__half> sv, FieldRef<__half> p,
+                                                        long npairs, int Lh) {
+  const float b = (float)(*beta);
+  for (long pi = (long)blockIdx.x * blockDim.x + threadIdx.x; pi < npairs; pi += (long)gridDim.x * blockDim.x) {
+    const long h = pi / Lh;
+    const int j = (int)(pi - h * Lh);
+    float2 re[12], im[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      const long c = (h * 12 + k) * Lh + j;
+      float a[4], d[4];
+      ld_chunk(sv, c, Lh, a);
+      ld_chunk(CFieldRef<__half>{p.v, p.norm}, c, Lh, d);
+      re[k] = make_float2(fmaf(b, d[0], a[0]), fmaf(b, d[1], a[1]));
+      im[k] = make_float2(fmaf(b, d[2], a[2]), fmaf(b, d[3], a[3]));
+    }
+    store_pair(p, h, j, Lh, re, im);
   }
 }
 
@@ -141,8 +242,7 @@ __global__ void k_alpha(const double* partials, int nb, double* num, double* den
 }
 
 // rr = sum(pr); ss = sum(ps); beta = ss / gam; gam = ss
-__global__ void k_beta(const double* pr, int nbr, const double* ps, int nbs, double* rr, double* gam,
-                       double* beta) {
+__global__ void k_beta(const double* pr, int nbr, const double* ps, int nbs, double* rr, double* gam, double* beta) {
   __shared__ double red[32];
   double a = 0.0, b = 0.0;
   for (int i = threadIdx.x; i < nbr; i += blockDim.x) a += pr[i];
@@ -158,20 +258,17 @@ __global__ void k_beta(const double* pr, int nbr, const double* ps, int nbs, dou
 
 }  // namespace
 
-#define DISPATCH1(prec, FN, ...)                            \
-  switch (prec) {                                            \
-    case DWF_F64: FN<double>(__VA_ARGS__); break;            \
-    case DWF_F32: FN<float>(__VA_ARGS__); break;             \
-    case DWF_F16: FN<__half>(__VA_ARGS__); break;            \
-  }
-
-template <class S> static void norm2_t(dwf_lattice* L, Field x, double* partials, int g) {
-  k_norm2<S><<<g, kBlasThreads, 0, L->stream>>>(cr<S>(x), L->Vh * L->Ls, L->Ls, partials);
-}
+static long nchunks(const dwf_lattice* L) { return field_elems(L) / 4; }
+static long npairs(const dwf_lattice* L) { return L->Vh * L->Lh; }
 
 dwf_status blas_norm2(dwf_lattice* L, Field x, double* partials, int* nb) {
-  const int g = grid_for(L->Vh * L->Ls);
-  DISPATCH1(x.prec, norm2_t, L, x, partials, g);
+  const long n = nchunks(L);
+  const int g = grid_for(n);
+  switch (x.prec) {
+    case DWF_F64: k_norm2<double><<<g, kBlasThreads, 0, L->stream>>>(cr<double>(x), n, L->Lh, partials); break;
+    case DWF_F32: k_norm2<float><<<g, kBlasThreads, 0, L->stream>>>(cr<float>(x), n, L->Lh, partials); break;
+    case DWF_F16: k_norm2<__half><<<g, kBlasThreads, 0, L->stream>>>(cr<__half>(x), n, L->Lh, partials); break;
+  }
   *nb = g;
   DWF_LAUNCHED(L);
   return DWF_OK;
@@ -183,18 +280,21 @@ dwf_status blas_sum(dwf_lattice* L, const double* partials, int nb, double* dst)
   return DWF_OK;
 }
 
-template <class SX, class SY>
-static void axpby_t(dwf_lattice* L, double a, Field x, double b, Field y, int read_y) {
-  const long n = L->Vh * L->Ls;
-  k_axpby<SX, SY><<<grid_for(n), kBlasThreads, 0, L->stream>>>(a, cr<SX>(x), b, wr<SY>(y), n, L->Ls, read_y);
-}
-
 template <class SX>
 static void axpby_x(dwf_lattice* L, double a, Field x, double b, Field y, int read_y) {
+  const long nq = nchunks(L), np = npairs(L);
   switch (y.prec) {
-    case DWF_F64: axpby_t<SX, double>(L, a, x, b, y, read_y); break;
-    case DWF_F32: axpby_t<SX, float>(L, a, x, b, y, read_y); break;
-    case DWF_F16: axpby_t<SX, __half>(L, a, x, b, y, read_y); break;
+    case DWF_F64:
+      k_axpby_c<SX, double><<<grid_for(nq), kBlasThreads, 0, L->stream>>>(a, cr<SX>(x), b, wr<double>(y), nq, L->Lh,
+                                                                          read_y);
+      break;
+    case DWF_F32:
+      k_axpby_c<SX, float><<<grid_for(nq), kBlasThreads, 0, L->stream>>>(a, cr<SX>(x), b, wr<float>(y), nq, L->Lh,
+                                                                         read_y);
+      break;
+    case DWF_F16:
+      k_axpby_p<SX><<<grid_for(np), kBlasThreads, 0, L->stream>>>(a, cr<SX>(x), b, wr<__half>(y), np, L->Lh, read_y);
+      break;
   }
 }
 
@@ -211,23 +311,24 @@ static dwf_status axpby_any(dwf_lattice* L, double a, Field x, double b, Field y
 dwf_status blas_axpby(dwf_lattice* L, double a, Field x, double b, Field y) { return axpby_any(L, a, x, b, y, 1); }
 dwf_status blas_copy(dwf_lattice* L, Field x, Field y) { return axpby_any(L, 1.0, x, 0.0, y, 0); }
 dwf_status blas_zero(dwf_lattice* L, Field x) { return axpby_any(L, 0.0, x, 0.0, x, 0); }
-dwf_status blas_accum(dwf_lattice* L, Field x, Field y64) { return axpby_any(L, 1.0, x, 1.0, y64, 1); }
-
-template <class S, class SX>
-static void cg_xr_t(dwf_lattice* L, const double* alpha, Field p, Field q, Field x, Field r, double* partials, int g) {
-  k_cg_xr<S, SX><<<g, kBlasThreads, 0, L->stream>>>(alpha, cr<S>(p), cr<S>(q), wr<SX>(x), wr<S>(r),
-                                                     L->Vh * L->Ls, L->Ls, partials);
-}
+dwf_status blas_accum(dwf_lattice* L, Field x, Field y) { return axpby_any(L, 1.0, x, 1.0, y, 1); }
 
 dwf_status blas_cg_xr(dwf_lattice* L, const double* alpha, Field p, Field q, Field x, Field r, double* partials,
                       int* nb) {
-  const int g = grid_for(L->Vh * L->Ls);
+  const long nq = nchunks(L), np = npairs(L);
+  int g;
   if (p.prec == DWF_F64 && x.prec == DWF_F64) {
-    cg_xr_t<double, double>(L, alpha, p, q, x, r, partials, g);
+    g = grid_for(nq);
+    k_cg_xr_c<double, double><<<g, kBlasThreads, 0, L->stream>>>(alpha, cr<double>(p), cr<double>(q), wr<double>(x),
+                                                                  wr<double>(r), nq, L->Lh, partials);
   } else if (p.prec == DWF_F32 && x.prec == DWF_F32) {
-    cg_xr_t<float, float>(L, alpha, p, q, x, r, partials, g);
+    g = grid_for(nq);
+    k_cg_xr_c<float, float><<<g, kBlasThreads, 0, L->stream>>>(alpha, cr<float>(p), cr<float>(q), wr<float>(x),
+                                                                wr<float>(r), nq, L->Lh, partials);
   } else if (p.prec == DWF_F16 && x.prec == DWF_F32) {
-    cg_xr_t<__half, float>(L, alpha, p, q, x, r, partials, g);
+    g = grid_for(np);
+    k_cg_xr_p<<<g, kBlasThreads, 0, L->stream>>>(alpha, cr<__half>(p), cr<__half>(q), wr<float>(x), wr<__half>(r),
+                                                  np, L->Lh, partials);
   } else {
     return fail(L, DWF_ERR_INVALID_ARG, "cg_xr: unsupported precision pair");
   }
@@ -236,13 +337,19 @@ dwf_status blas_cg_xr(dwf_lattice* L, const double* alpha, Field p, Field q, Fie
   return DWF_OK;
 }
 
-template <class S> static void cg_p_t(dwf_lattice* L, const double* beta, Field s, Field p) {
-  const long n = L->Vh * L->Ls;
-  k_cg_p<S><<<grid_for(n), kBlasThreads, 0, L->stream>>>(beta, cr<S>(s), wr<S>(p), n, L->Ls);
-}
-
 dwf_status blas_cg_p(dwf_lattice* L, const double* beta, Field s, Field p) {
-  DISPATCH1(p.prec, cg_p_t, L, beta, s, p);
+  const long nq = nchunks(L), np = npairs(L);
+  switch (p.prec) {
+    case DWF_F64:
+      k_cg_p_c<double><<<grid_for(nq), kBlasThreads, 0, L->stream>>>(beta, cr<double>(s), wr<double>(p), nq, L->Lh);
+      break;
+    case DWF_F32:
+      k_cg_p_c<float><<<grid_for(nq), kBlasThreads, 0, L->stream>>>(beta, cr<float>(s), wr<float>(p), nq, L->Lh);
+      break;
+    case DWF_F16:
+      k_cg_p_p<<<grid_for(np), kBlasThreads, 0, L->stream>>>(beta, cr<__half>(s), wr<__half>(p), np, L->Lh);
+      break;
+  }
   DWF_LAUNCHED(L);
   return DWF_OK;
 }

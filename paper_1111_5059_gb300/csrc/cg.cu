@@ -186,6 +186,119 @@ dwf_status cg_core(dwf_lattice* L, const SOps* ops, Field bp, Field x64, double 
   return DWF_OK;
 }
 
+// CG on the normal operator: solve M~^+ M~ x64 = v to |v - M~^+ M~ x| <= tol |v|
+// (the force solve X = (M^+ M)^-1 M2^+ phi of Sec. 2-3).  x64 holds the guess.
+// Same reliable-update scheme as cg_core.
+dwf_status cgne_core(dwf_lattice* L, const SOps* ops, Field v, Field x64, const dwf_cg_params& prm, dwf_stats* st,
+                     long long* hops) {
+  const dwf_prec ip = prm.inner;
+  Op o{L, ops, hops};
+  Field r64, w64, u64;
+  DWF_TRY(field_alloc(L, "ne.r64", DWF_F64, &r64));
+  DWF_TRY(field_alloc(L, "ne.w64", DWF_F64, &w64));
+  DWF_TRY(field_alloc(L, "ne.u64", DWF_F64, &u64));
+  const bool mixed = ip != DWF_F64;
+  Field x, r, p, w, q, u;
+  if (mixed) {
+    DWF_TRY(field_alloc(L, "ne.x", ip == DWF_F16 ? DWF_F32 : ip, &x));
+    DWF_TRY(field_alloc(L, "ne.r", ip, &r));
+    DWF_TRY(field_alloc(L, "ne.u", ip, &u));
+    DWF_TRY(field_alloc(L, "ne.w", ip, &w));
+  } else {
+    x = x64;
+    r = r64;
+    u = u64;
+    w = w64;
+  }
+  DWF_TRY(field_alloc(L, "ne.p", ip, &p));
+  DWF_TRY(field_alloc(L, "ne.q", ip, &q));
+  double* pr = L->partials;
+  double* sc = L->scal;
+  int nb;
+  DWF_TRY(blas_norm2(L, v, pr, &nb));
+  DWF_TRY(blas_sum(L, pr, nb, sc + S_TMP1));
+  DWF_TRY(fetch_scalars(L));
+  const double vv = L->hscal[S_TMP1];
+  if (!std::isfinite(vv)) return fail(L, DWF_ERR_NAN, "cgne: non-finite right-hand side");
+  if (vv == 0.0) {
+    DWF_TRY(blas_zero(L, x64));
+    st->true_resid = 0.0;
+    return DWF_OK;
+  }
+  const double tol2 = prm.tol * prm.tol * vv;
+  const double delta2 = prm.delta * prm.delta;
+  const int check = prm.check_every < 1 ? 1 : prm.check_every;
+  // r64 = v - M~^+ M~ x64
+  auto true_res = [&](double* rr) -> dwf_status {
+    DWF_TRY(apply_Mt(o, false, x64, w64, u64, nullptr, nullptr));
+    DWF_TRY(apply_Mt(o, true, w64, r64, u64, nullptr, nullptr));
+    DWF_TRY(blas_axpby(L, 1.0, v, -1.0, r64));
+    int n2;
+    DWF_TRY(blas_norm2(L, r64, pr, &n2));
+    DWF_TRY(blas_sum(L, pr, n2, sc + S_TMP0));
+    DWF_TRY(fetch_scalars(L));
+    *rr = L->hscal[S_TMP0];
+    return DWF_OK;
+  };
+  double rr64;
+  DWF_TRY(true_res(&rr64));
+  if (!std::isfinite(rr64)) return fail(L, DWF_ERR_NAN, "cgne: non-finite initial residual");
+  if (rr64 <= tol2) {
+    st->true_resid = std::sqrt(rr64 / vv);
+    return DWF_OK;
+  }
+  if (mixed) {
+    DWF_TRY(blas_copy(L, r64, r));
+    DWF_TRY(blas_zero(L, x));
+  }
+  DWF_TRY(blas_copy(L, r, p));
+  DWF_TRY(blas_norm2(L, r, pr, &nb));
+  DWF_TRY(blas_sum(L, pr, nb, sc + S_GAM));  // gam = |r|^2
+  double maxrr = rr64;
+  int it = 0;
+  while (true) {
+    int nw, nr;
+    DWF_TRY(apply_Mt(o, false, p, w, u, pr, &nw));  // |w|^2 = <p, N p>
+    DWF_TRY(scal_alpha(L, pr, nw, sc + S_GAM, sc + S_QQ, sc + S_ALPHA));
+    DWF_TRY(apply_Mt(o, true, w, q, u, nullptr, nullptr));
+    DWF_TRY(blas_cg_xr(L, sc + S_ALPHA, p, q, x, r, pr, &nr));
+    DWF_TRY(scal_beta(L, pr, nr, pr, nr, sc + S_RR, sc + S_GAM, sc + S_BETA));
+    DWF_TRY(blas_cg_p(L, sc + S_BETA, r, p));
+    ++it;
+    const bool last = it >= prm.max_iter;
+    if (it % check != 0 && !last) continue;
+    DWF_TRY(fetch_scalars(L));
+    const double rr = L->hscal[S_RR];
+    if (!std::isfinite(rr)) {
+      st->iters += it;
+      return fail(L, DWF_ERR_NAN, "cgne: non-finite residual norm");
+    }
+    if (rr <= tol2 || (mixed && rr < delta2 * maxrr) || last) {
+      if (mixed) {
+        DWF_TRY(blas_accum(L, x, x64));
+        DWF_TRY(blas_zero(L, x));
+      }
+      DWF_TRY(true_res(&rr64));
+      ++st->reliable_updates;
+      if (rr64 <= tol2) break;
+      if (last) {
+        st->iters += it;
+        st->true_resid = std::sqrt(rr64 / vv);
+        return fail(L, DWF_ERR_NOT_CONVERGED, "cgne: max_iter reached");
+      }
+      if (mixed) DWF_TRY(blas_copy(L, r64, r));
+      DWF_TRY(blas_norm2(L, r, pr, &nb));
+      DWF_TRY(blas_sum(L, pr, nb, sc + S_GAM));
+      maxrr = rr64;
+    } else if (rr > maxrr) {
+      maxrr = rr;
+    }
+  }
+  st->iters += it;
+  st->true_resid = std::sqrt(rr64 / vv);
+  return DWF_OK;
+}
+
 // Full solve on FP64 parity fields: b (be, bo) -> x (xe, xo; xe holds the guess).
 dwf_status solve_eo(dwf_lattice* L, double m, Field be, Field bo, Field xe, Field xo, const dwf_cg_params& prm,
                     dwf_stats* st, double* true_res_full) {

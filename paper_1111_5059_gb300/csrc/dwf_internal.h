@@ -1,17 +1,22 @@
 // Internal declarations of the GB300 domain-wall library (not part of the ABI).
 //
 // Internal layouts (one checkerboard, "half" lattice of Vh = V4/2 sites):
-//   spinor  : chunks of 16 bytes, index ((h * NC + c) * Ls + s), s fastest, so
-//             the Ls threads of a 4D site read consecutive 16-byte words.
-//             FP64: NC = 12 chunks of one complex; FP32: NC = 6 chunks of two
-//             complex; FP16: NC = 3 chunks of four complex plus one float
-//             scale per (h, s).  Complex component k = spin * 3 + colour.
+//   spinor  : the Ls slices of a 4D site are split into Lh = ceil(Ls/2) pairs
+//             (j, j + Lh).  Element order [h][k][j][4] with the 4 elements
+//             (re s0, re s1, im s0, im s1), s0 = j, s1 = j + Lh, complex
+//             component k = spin * 3 + colour (spins 0,1 = P+ half).  One
+//             16-byte FP32 chunk therefore holds one complex component of two
+//             slices, so a thread owning the pair (h, j) computes both slices
+//             with packed FP32x2 instructions, and the Ls / 2 threads of a
+//             site read consecutive chunks.  All precisions share the element
+//             order (FP64: 32-byte chunks; FP16: 8-byte chunks plus one FP32
+//             scale per (h, slice), stored [h][j][2]), so precision casts and
+//             level-1 kernels are flat element-wise loops.  For odd Ls the
+//             slot s1 = Ls of the last pair is padding and is kept zero.
 //   links   : per output parity, [Vh][8][18] reals: directions 0..3 are
 //             U_mu(n), 4..7 are U_mu(n - mu)^+, t boundary phase folded in.
 //   nbr     : per output parity, int32 [8][Vh] half-site index of the
 //             neighbour n + mu (d < 4) or n - mu (d >= 4) on the other parity.
-//   s-ops   : fifth-dimension operators, two real Ls x Ls matrices
-//             (P+ block, P- block), row-major, in FP64 and FP32.
 #pragma once
 
 #include <cuda_fp16.h>
@@ -34,102 +39,137 @@ constexpr int kBlasThreads = 256;
 
 template <class S> struct Store;
 template <> struct Store<double> {
-  typedef double2 chunk_t;
   typedef double calc_t;
-  static constexpr int NC = 12;
-  static constexpr int PER = 1;  // complex per chunk
 };
 template <> struct Store<float> {
-  typedef float4 chunk_t;
   typedef float calc_t;
-  static constexpr int NC = 6;
-  static constexpr int PER = 2;
 };
 template <> struct Store<__half> {
-  typedef uint4 chunk_t;
   typedef float calc_t;
-  static constexpr int NC = 3;
-  static constexpr int PER = 4;
 };
 
-// A one-parity spinor field of storage type S.
+// A one-parity spinor field of storage type S (norm: FP16 only, [Vh][Lh][2]).
 template <class S> struct FieldRef {
-  typename Store<S>::chunk_t* v;
-  float* norm;  // FP16 only: per (h, s) scale
+  S* v;
+  float* norm;
 };
 template <class S> struct CFieldRef {
-  const typename Store<S>::chunk_t* v;
+  const S* v;
   const float* norm;
 };
 
-// ---------------------------------------------------------------- spinor io
+__device__ __forceinline__ float to_f(__half x) { return __half2float(x); }
+__device__ __forceinline__ float to_f(float x) { return x; }
+__device__ __forceinline__ double to_f(double x) { return x; }
 
-__device__ __forceinline__ void load_chunk(const double2* p, double* out) {
-  double2 a = __ldg(p);
-  out[0] = a.x;
-  out[1] = a.y;
-}
-__device__ __forceinline__ void load_chunk(const float4* p, float* out) {
-  float4 a = __ldg(p);
-  out[0] = a.x;
-  out[1] = a.y;
-  out[2] = a.z;
-  out[3] = a.w;
+// ---------------------------------------------------------------- per-slice spinor io
+// (h, s) access: 24 reals of slice s of site h; used by the kernels that are not
+// bandwidth-critical (packing, s-local operators, the FP64 hop).
+
+__host__ __device__ __forceinline__ long elem_index(long h, int k, int j, int Lh) {
+  return (((long)h * 12 + k) * Lh + j) * 4;
 }
 
-// Load the 24 reals of spinor (h, s).
 template <class S>
-__device__ __forceinline__ void load_spinor(CFieldRef<S> f, long h, int s, int Ls,
+__device__ __forceinline__ void load_spinor(CFieldRef<S> f, long h, int s, int Lh,
                                             typename Store<S>::calc_t* v) {
-  constexpr int NC = Store<S>::NC;
-  if constexpr (sizeof(S) == 2) {
-    const float sc = __ldg(f.norm + h * Ls + s);
+  typedef typename Store<S>::calc_t C;
+  const int half = s >= Lh ? 1 : 0;
+  const int j = s - half * Lh;
+  const S* base = f.v + elem_index(h, 0, j, Lh) + half;
+  C sc = 1;
+  if constexpr (sizeof(S) == 2) sc = __ldg(f.norm + ((long)h * Lh + j) * 2 + half);
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      uint4 a = __ldg(f.v + (h * NC + c) * Ls + s);
-      const __half2* hp = reinterpret_cast<const __half2*>(&a);
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        float2 t = __half22float2(hp[j]);
-        v[8 * c + 2 * j] = t.x * sc;
-        v[8 * c + 2 * j + 1] = t.y * sc;
-      }
-    }
-  } else {
-    constexpr int R = 2 * Store<S>::PER;
-#pragma unroll
-    for (int c = 0; c < NC; ++c) load_chunk(f.v + (h * NC + c) * Ls + s, v + R * c);
+  for (int k = 0; k < 12; ++k) {
+    v[2 * k] = (C)to_f(base[(long)k * Lh * 4]) * sc;
+    v[2 * k + 1] = (C)to_f(base[(long)k * Lh * 4 + 2]) * sc;
   }
 }
 
+// FP16: a slice whose largest component is below the normal FP32 range is
+// stored as zero (1/max would overflow and turn exact zeros into NaN).
+__device__ __forceinline__ float half_scale(float mx, float* inv) {
+  const bool keep = mx >= 1.17549435e-38f;
+  *inv = keep ? 1.0f / mx : 0.f;
+  return keep ? mx : 0.f;
+}
+
 template <class S>
-__device__ __forceinline__ void store_spinor(FieldRef<S> f, long h, int s, int Ls,
+__device__ __forceinline__ void store_spinor(FieldRef<S> f, long h, int s, int Lh,
                                              const typename Store<S>::calc_t* v) {
-  constexpr int NC = Store<S>::NC;
-  if constexpr (sizeof(S) == 8) {
-#pragma unroll
-    for (int c = 0; c < NC; ++c) f.v[(h * NC + c) * Ls + s] = make_double2(v[2 * c], v[2 * c + 1]);
-  } else if constexpr (sizeof(S) == 4) {
-#pragma unroll
-    for (int c = 0; c < NC; ++c)
-      f.v[(h * NC + c) * Ls + s] = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
-  } else {
+  const int half = s >= Lh ? 1 : 0;
+  const int j = s - half * Lh;
+  S* base = f.v + elem_index(h, 0, j, Lh) + half;
+  if constexpr (sizeof(S) == 2) {
     float mx = 0.f;
 #pragma unroll
     for (int k = 0; k < 24; ++k) mx = fmaxf(mx, fabsf(v[k]));
-    // A site whose largest component is below the normal FP32 range is
-    // stored as zero (1/mx would overflow and turn exact zeros into NaN).
-    const bool keep = mx >= 1.17549435e-38f;
-    const float inv = keep ? 1.0f / mx : 0.f;
-    f.norm[h * Ls + s] = keep ? mx : 0.f;
+    float inv;
+    f.norm[((long)h * Lh + j) * 2 + half] = half_scale(mx, &inv);
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      uint4 a;
-      __half2* hp = reinterpret_cast<__half2*>(&a);
-#pragma unroll
-      for (int j = 0; j < 4; ++j) hp[j] = __floats2half2_rn(v[8 * c + 2 * j] * inv, v[8 * c + 2 * j + 1] * inv);
-      f.v[(h * NC + c) * Ls + s] = a;
+    for (int k = 0; k < 12; ++k) {
+      base[(long)k * Lh * 4] = __float2half_rn(v[2 * k] * inv);
+      base[(long)k * Lh * 4 + 2] = __float2half_rn(v[2 * k + 1] * inv);
     }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      base[(long)k * Lh * 4] = (S)v[2 * k];
+      base[(long)k * Lh * 4 + 2] = (S)v[2 * k + 1];
+    }
+  }
+}
+
+// ---------------------------------------------------------------- per-pair io (FP32 arithmetic)
+// re[k] = (re s0, re s1), im[k] = (im s0, im s1) of site h, pair j.
+
+__device__ __forceinline__ void load_pair(CFieldRef<float> f, long h, int j, int Lh, float2* re, float2* im) {
+  const float4* p = reinterpret_cast<const float4*>(f.v) + ((long)h * 12) * Lh + j;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    const float4 a = __ldg(p + (long)k * Lh);
+    re[k] = make_float2(a.x, a.y);
+    im[k] = make_float2(a.z, a.w);
+  }
+}
+__device__ __forceinline__ void load_pair(CFieldRef<__half> f, long h, int j, int Lh, float2* re, float2* im) {
+  const uint2* p = reinterpret_cast<const uint2*>(f.v) + ((long)h * 12) * Lh + j;
+  const float2 sc = __ldg(reinterpret_cast<const float2*>(f.norm) + (long)h * Lh + j);
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    const uint2 a = __ldg(p + (long)k * Lh);
+    const float2 r = __half22float2(*reinterpret_cast<const __half2*>(&a.x));
+    const float2 i = __half22float2(*reinterpret_cast<const __half2*>(&a.y));
+    re[k] = make_float2(r.x * sc.x, r.y * sc.y);
+    im[k] = make_float2(i.x * sc.x, i.y * sc.y);
+  }
+}
+__device__ __forceinline__ void store_pair(FieldRef<float> f, long h, int j, int Lh, const float2* re,
+                                           const float2* im) {
+  float4* p = reinterpret_cast<float4*>(f.v) + ((long)h * 12) * Lh + j;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) p[(long)k * Lh] = make_float4(re[k].x, re[k].y, im[k].x, im[k].y);
+}
+__device__ __forceinline__ void store_pair(FieldRef<__half> f, long h, int j, int Lh, const float2* re,
+                                           const float2* im) {
+  float m0 = 0.f, m1 = 0.f;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    m0 = fmaxf(m0, fmaxf(fabsf(re[k].x), fabsf(im[k].x)));
+    m1 = fmaxf(m1, fmaxf(fabsf(re[k].y), fabsf(im[k].y)));
+  }
+  float i0, i1;
+  const float n0 = half_scale(m0, &i0), n1 = half_scale(m1, &i1);
+  reinterpret_cast<float2*>(f.norm)[(long)h * Lh + j] = make_float2(n0, n1);
+  uint2* p = reinterpret_cast<uint2*>(f.v) + ((long)h * 12) * Lh + j;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    const __half2 r = __floats2half2_rn(re[k].x * i0, re[k].y * i1);
+    const __half2 i = __floats2half2_rn(im[k].x * i0, im[k].y * i1);
+    uint2 a;
+    a.x = *reinterpret_cast<const unsigned*>(&r);
+    a.y = *reinterpret_cast<const unsigned*>(&i);
+    p[(long)k * Lh] = a;
   }
 }
 
@@ -210,16 +250,17 @@ struct dwf_lattice {
   dwf_params p;
   int X, Y, Z, T;
   long V4, Vh;
-  int Ls;
+  int Ls, Lh;  // Lh = ceil(Ls / 2) slice pairs
   cudaStream_t stream;
   int* nbr[2] = {nullptr, nullptr};
   void* links[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
   bool gauge_set = false;
   std::deque<dwf::SOps> sops;  // deque: pointers stay valid on growth
   std::map<std::string, dwf::Buffer> ws;
-  double* partials = nullptr;  // device, kPartials doubles
+  double* partials = nullptr;  // device, 2 * kPartials doubles
   double* scal = nullptr;      // device scalars
   double* hscal = nullptr;     // pinned host mirror
+  int* dev_err = nullptr;      // device error flag (bounded waits that gave up)
   std::string err;
   // instrumentation
   long long launches = 0;  // every kernel this handle has launched
@@ -243,21 +284,21 @@ constexpr int kScalars = 64;
 // error helpers (lattice.cu)
 dwf_status fail(dwf_lattice* L, dwf_status st, const std::string& msg);
 dwf_status cuda_check(dwf_lattice* L, cudaError_t e, const char* what);
-#define DWF_CUDA(L, call)                                           \
-  do {                                                              \
-    cudaError_t _e = (call);                                        \
+#define DWF_CUDA(L, call)                                            \
+  do {                                                               \
+    cudaError_t _e = (call);                                         \
     if (_e != cudaSuccess) return ::dwf::cuda_check((L), _e, #call); \
   } while (0)
 // after exactly one kernel launch: count it and check the launch
-#define DWF_LAUNCHED(L)         \
-  do {                          \
-    ::dwf::counted(L);          \
+#define DWF_LAUNCHED(L)              \
+  do {                               \
+    ::dwf::counted(L);               \
     DWF_CUDA(L, cudaGetLastError()); \
   } while (0)
-#define DWF_TRY(call)                   \
-  do {                                  \
-    dwf_status _s = (call);             \
-    if (_s != DWF_OK) return _s;        \
+#define DWF_TRY(call)            \
+  do {                           \
+    dwf_status _s = (call);      \
+    if (_s != DWF_OK) return _s; \
   } while (0)
 
 // instrumentation (lattice.cu)
@@ -268,7 +309,8 @@ dwf_status timing_drain(dwf_lattice* L);  // stream must be idle
 
 // workspace (lattice.cu)
 dwf_status ws_get(dwf_lattice* L, const std::string& name, size_t bytes, void** out);
-size_t field_bytes(const dwf_lattice* L, dwf_prec prec);  // one parity, excluding FP16 norms
+long field_elems(const dwf_lattice* L);                   // reals per one-parity field, incl. padding
+size_t field_bytes(const dwf_lattice* L, dwf_prec prec);  // excluding FP16 scales
 const SOps* sops_for(dwf_lattice* L, double m, dwf_status* st);
 
 // one-parity field handle used by the host drivers
@@ -277,7 +319,10 @@ struct Field {
   float* norm = nullptr;
   dwf_prec prec = DWF_F64;
 };
+// Allocates (first use: zero-filled, so odd-Ls padding starts at zero).
 dwf_status field_alloc(dwf_lattice* L, const std::string& name, dwf_prec prec, Field* f);
+// Checks and clears the device error flag (after the stream is idle).
+dwf_status check_dev_err(dwf_lattice* L);
 
 // ---------------------------------------------------------------- kernels (launchers)
 
@@ -307,23 +352,23 @@ dwf_status launch_pack(dwf_lattice* L, const void* boundary, int parity, Field o
 dwf_status launch_unpack(dwf_lattice* L, Field in, int parity, void* boundary, bool zero_other);
 dwf_status launch_pack_gauge(dwf_lattice* L, const void* U);
 
-// blas.cu (all on one-parity fields of L; n = Vh * Ls * 24 reals)
-// Reductions write per-block partials; finalise with launch_sum.
+// blas.cu (one-parity fields of L).  Reductions write per-block partials;
+// finalise with blas_sum / scal_*.
 dwf_status blas_norm2(dwf_lattice* L, Field x, double* partials, int* nb);
 dwf_status blas_sum(dwf_lattice* L, const double* partials, int nb, double* dst);  // device dst
 dwf_status blas_copy(dwf_lattice* L, Field x, Field y);                             // y = x (any precisions)
 dwf_status blas_zero(dwf_lattice* L, Field x);
-// y = a*x + b*y with host scalars
+// y = a*x + b*y with host scalars (any precisions)
 dwf_status blas_axpby(dwf_lattice* L, double a, Field x, double b, Field y);
 // CG steps with device scalars (pointers into L->scal)
 dwf_status blas_cg_xr(dwf_lattice* L, const double* alpha, Field p, Field q, Field x, Field r,
-                      double* partials, int* nb);                   // x += a p; r -= a q; |r|^2
+                      double* partials, int* nb);  // x += a p; r -= a q; |r|^2
 dwf_status blas_cg_p(dwf_lattice* L, const double* beta, Field s, Field p);  // p = s + b p
-// add a low-precision field into a FP64 one: y64 += x
-dwf_status blas_accum(dwf_lattice* L, Field x, Field y64);
+// add a lower-precision field into another: y += x
+dwf_status blas_accum(dwf_lattice* L, Field x, Field y);
 // scalar kernels
 dwf_status scal_alpha(dwf_lattice* L, const double* partials, int nb, double* num, double* den, double* alpha);
-dwf_status scal_beta(dwf_lattice* L, const double* pr, int nbr, const double* ps, int nbs,
-                     double* rr, double* gam, double* beta);
+dwf_status scal_beta(dwf_lattice* L, const double* pr, int nbr, const double* ps, int nbs, double* rr,
+                     double* gam, double* beta);
 
 }  // namespace dwf

@@ -26,9 +26,20 @@ dwf_status cuda_check(dwf_lattice* L, cudaError_t e, const char* what) {
   return fail(L, e == cudaErrorMemoryAllocation ? DWF_ERR_OOM : DWF_ERR_CUDA, msg);
 }
 
+long field_elems(const dwf_lattice* L) { return L->Vh * 12 * L->Lh * 4; }
+
 size_t field_bytes(const dwf_lattice* L, dwf_prec prec) {
-  const size_t sites = (size_t)L->Vh * L->Ls;
-  return sites * 24 * (prec == DWF_F64 ? 8 : prec == DWF_F32 ? 4 : 2);
+  return (size_t)field_elems(L) * (prec == DWF_F64 ? 8 : prec == DWF_F32 ? 4 : 2);
+}
+
+dwf_status check_dev_err(dwf_lattice* L) {
+  int h = 0;
+  DWF_CUDA(L, cudaMemcpy(&h, L->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (h != 0) {
+    DWF_CUDA(L, cudaMemset(L->dev_err, 0, sizeof(int)));
+    return fail(L, DWF_ERR_TIMEOUT, "a bounded device wait gave up (asynchronous copy did not complete)");
+  }
+  return DWF_OK;
 }
 
 dwf_status ws_get(dwf_lattice* L, const std::string& name, size_t bytes, void** out) {
@@ -44,6 +55,12 @@ dwf_status ws_get(dwf_lattice* L, const std::string& name, size_t bytes, void** 
   void* p = nullptr;
   cudaError_t e = cudaMalloc(&p, bytes);
   if (e != cudaSuccess) return cuda_check(L, e, ("workspace " + name).c_str());
+  // zero-filled once: padding slots of odd-Ls fields must read as zero
+  e = cudaMemsetAsync(p, 0, bytes, L->stream);
+  if (e != cudaSuccess) {
+    cudaFree(p);
+    return cuda_check(L, e, ("workspace clear " + name).c_str());
+  }
   L->ws[name] = Buffer{p, bytes};
   *out = p;
   return DWF_OK;
@@ -55,7 +72,7 @@ dwf_status field_alloc(dwf_lattice* L, const std::string& name, dwf_prec prec, F
   DWF_TRY(ws_get(L, name, field_bytes(L, prec), &f->v));
   if (prec == DWF_F16) {
     void* n = nullptr;
-    DWF_TRY(ws_get(L, name + ".norm", (size_t)L->Vh * L->Ls * sizeof(float), &n));
+    DWF_TRY(ws_get(L, name + ".norm", (size_t)L->Vh * L->Lh * 2 * sizeof(float), &n));
     f->norm = reinterpret_cast<float*>(n);
   }
   return DWF_OK;
@@ -248,7 +265,7 @@ __device__ __forceinline__ long full_site(const Geo& g, long h, int parity, int*
 }
 
 template <class S>
-__global__ void pack_kernel(const double2* __restrict__ bnd, Geo g, int Ls, int parity, FieldRef<S> out) {
+__global__ void pack_kernel(const double2* __restrict__ bnd, Geo g, int Ls, int Lh, int parity, FieldRef<S> out) {
   const long q = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= g.Vh * Ls) return;
   const long h = q / Ls;
@@ -263,11 +280,11 @@ __global__ void pack_kernel(const double2* __restrict__ bnd, Geo g, int Ls, int 
     v[2 * k] = (typename Store<S>::calc_t)a.x;
     v[2 * k + 1] = (typename Store<S>::calc_t)a.y;
   }
-  store_spinor<S>(out, h, s, Ls, v);
+  store_spinor<S>(out, h, s, Lh, v);
 }
 
 template <class S>
-__global__ void unpack_kernel(CFieldRef<S> in, Geo g, int Ls, int parity, double2* __restrict__ bnd,
+__global__ void unpack_kernel(CFieldRef<S> in, Geo g, int Ls, int Lh, int parity, double2* __restrict__ bnd,
                               int zero_other) {
   const long q = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= g.Vh * Ls) return;
@@ -276,7 +293,7 @@ __global__ void unpack_kernel(CFieldRef<S> in, Geo g, int Ls, int parity, double
   const long n = full_site(g, h, parity, nullptr);
   const long V4 = 2 * g.Vh;
   typename Store<S>::calc_t v[24];
-  load_spinor<S>(in, h, s, Ls, v);
+  load_spinor<S>(in, h, s, Lh, v);
   double2* dst = bnd + ((long)s * V4 + n) * 12;
 #pragma unroll
   for (int k = 0; k < 12; ++k) dst[k] = make_double2((double)v[2 * k], (double)v[2 * k + 1]);
@@ -326,21 +343,20 @@ __global__ void pack_gauge_kernel(const double2* __restrict__ U, Geo g, int bc_t
 
 static Geo geo(const dwf_lattice* L) { return Geo{L->X, L->Y, L->Z, L->T, L->Vh}; }
 
-template <class S> static FieldRef<S> fref(Field f) {
-  return FieldRef<S>{reinterpret_cast<typename Store<S>::chunk_t*>(f.v), f.norm};
-}
+template <class S> static FieldRef<S> fref(Field f) { return FieldRef<S>{reinterpret_cast<S*>(f.v), f.norm}; }
 template <class S> static CFieldRef<S> cfref(Field f) {
-  return CFieldRef<S>{reinterpret_cast<const typename Store<S>::chunk_t*>(f.v), f.norm};
+  return CFieldRef<S>{reinterpret_cast<const S*>(f.v), f.norm};
 }
 
 dwf_status launch_pack(dwf_lattice* L, const void* bnd, int parity, Field out) {
   const long n = L->Vh * L->Ls;
   const unsigned blocks = (unsigned)((n + 255) / 256);
   const double2* b = reinterpret_cast<const double2*>(bnd);
+  const int Ls = L->Ls, Lh = L->Lh;
   switch (out.prec) {
-    case DWF_F64: pack_kernel<double><<<blocks, 256, 0, L->stream>>>(b, geo(L), L->Ls, parity, fref<double>(out)); break;
-    case DWF_F32: pack_kernel<float><<<blocks, 256, 0, L->stream>>>(b, geo(L), L->Ls, parity, fref<float>(out)); break;
-    case DWF_F16: pack_kernel<__half><<<blocks, 256, 0, L->stream>>>(b, geo(L), L->Ls, parity, fref<__half>(out)); break;
+    case DWF_F64: pack_kernel<double><<<blocks, 256, 0, L->stream>>>(b, geo(L), Ls, Lh, parity, fref<double>(out)); break;
+    case DWF_F32: pack_kernel<float><<<blocks, 256, 0, L->stream>>>(b, geo(L), Ls, Lh, parity, fref<float>(out)); break;
+    case DWF_F16: pack_kernel<__half><<<blocks, 256, 0, L->stream>>>(b, geo(L), Ls, Lh, parity, fref<__half>(out)); break;
   }
   DWF_LAUNCHED(L);
   return DWF_OK;
@@ -350,10 +366,11 @@ dwf_status launch_unpack(dwf_lattice* L, Field in, int parity, void* bnd, bool z
   const long n = L->Vh * L->Ls;
   const unsigned blocks = (unsigned)((n + 255) / 256);
   double2* b = reinterpret_cast<double2*>(bnd);
+  const int Ls = L->Ls, Lh = L->Lh;
   switch (in.prec) {
-    case DWF_F64: unpack_kernel<double><<<blocks, 256, 0, L->stream>>>(cfref<double>(in), geo(L), L->Ls, parity, b, zero_other); break;
-    case DWF_F32: unpack_kernel<float><<<blocks, 256, 0, L->stream>>>(cfref<float>(in), geo(L), L->Ls, parity, b, zero_other); break;
-    case DWF_F16: unpack_kernel<__half><<<blocks, 256, 0, L->stream>>>(cfref<__half>(in), geo(L), L->Ls, parity, b, zero_other); break;
+    case DWF_F64: unpack_kernel<double><<<blocks, 256, 0, L->stream>>>(cfref<double>(in), geo(L), Ls, Lh, parity, b, zero_other); break;
+    case DWF_F32: unpack_kernel<float><<<blocks, 256, 0, L->stream>>>(cfref<float>(in), geo(L), Ls, Lh, parity, b, zero_other); break;
+    case DWF_F16: unpack_kernel<__half><<<blocks, 256, 0, L->stream>>>(cfref<__half>(in), geo(L), Ls, Lh, parity, b, zero_other); break;
   }
   DWF_LAUNCHED(L);
   return DWF_OK;
@@ -519,6 +536,7 @@ dwf_status dwf_create_lattice(const dwf_params* p, void* stream, dwf_lattice_t* 
   L->V4 = V4;
   L->Vh = V4 / 2;
   L->Ls = p->Ls;
+  L->Lh = (p->Ls + 1) / 2;
   L->stream = reinterpret_cast<cudaStream_t>(stream);
   // neighbour tables
   std::vector<int> nb((size_t)8 * L->Vh);
@@ -554,6 +572,8 @@ dwf_status dwf_create_lattice(const dwf_params* p, void* stream, dwf_lattice_t* 
   if (e == cudaSuccess) e = cudaMalloc(&L->scal, kScalars * sizeof(double));
   if (e == cudaSuccess) e = cudaMallocHost(&L->hscal, kScalars * sizeof(double));
   if (e == cudaSuccess) e = cudaMemset(L->scal, 0, kScalars * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&L->dev_err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(L->dev_err, 0, sizeof(int));
   if (e != cudaSuccess) {
     dwf_status st = cuda_check(nullptr, e, "lattice scratch");
     dwf_destroy_lattice(L);
@@ -576,6 +596,7 @@ dwf_status dwf_destroy_lattice(dwf_lattice_t L) {
   for (auto& kv : L->ws) cudaFree(kv.second.p);
   cudaFree(L->partials);
   cudaFree(L->scal);
+  cudaFree(L->dev_err);
   cudaFreeHost(L->hscal);
   for (auto& p : L->pending) {
     cudaEventDestroy(p.a);

@@ -48,6 +48,29 @@ class Stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+MADWF_MAX_PASSES = 16
+
+
+class MadwfParams(ctypes.Structure):
+    _fields_ = [("n_dc", ctypes.c_int), ("tol_pv", ctypes.c_double), ("tol_mob", ctypes.c_double),
+                ("tol_final", ctypes.c_double), ("inner", ctypes.c_int), ("max_iter", ctypes.c_int),
+                ("delta", ctypes.c_double), ("check_every", ctypes.c_int)]
+
+
+class MadwfStats(ctypes.Structure):
+    _fields_ = [("total", Stats), ("pv", Stats), ("mobius", Stats), ("final_cg", Stats),
+                ("passes", ctypes.c_int), ("pass_resid", ctypes.c_double * MADWF_MAX_PASSES)]
+
+    def as_dict(self):
+        return {"total": self.total.as_dict(), "pv": self.pv.as_dict(), "mobius": self.mobius.as_dict(),
+                "final_cg": self.final_cg.as_dict(), "passes": self.passes,
+                "pass_resid": [self.pass_resid[i] for i in range(self.passes)]}
+
+
+class Quotient(ctypes.Structure):
+    _fields_ = [("m1", ctypes.c_double), ("m2", ctypes.c_double)]
+
+
 _lib = None
 _VP = ctypes.c_void_p
 
@@ -63,6 +86,14 @@ def _declare(lib):
         "dwf_apply_MdagM": [H, ctypes.c_double, _VP, _VP],
         "dwf_apply_Mpc": [H, ctypes.c_double, ctypes.c_int, _VP, _VP],
         "dwf_cg": [H, ctypes.c_double, _VP, _VP, ctypes.POINTER(CGParams), ctypes.POINTER(Stats)],
+        "madwf_solve": [H, H, ctypes.c_double, _VP, _VP, ctypes.POINTER(MadwfParams), ctypes.POINTER(MadwfStats)],
+        "dwf_force": [H, ctypes.c_int, ctypes.POINTER(Quotient), ctypes.POINTER(_VP), ctypes.POINTER(_VP), _VP, _VP,
+                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(CGParams), ctypes.POINTER(Stats)],
+        "fgi_link_update": [H, _VP, ctypes.c_double, _VP, _VP],
+        "dwf_momentum_update": [H, _VP, ctypes.c_double, _VP],
+        "dwf_kinetic": [H, _VP, ctypes.POINTER(ctypes.c_double)],
+        "fgi_step": [H, ctypes.c_int, ctypes.POINTER(Quotient), ctypes.POINTER(_VP), _VP, _VP, ctypes.c_double,
+                     ctypes.c_int, ctypes.POINTER(CGParams), ctypes.POINTER(Stats), ctypes.POINTER(ctypes.c_int)],
         "dwf_set_kernel_timing": [H, ctypes.c_int],
         "dwf_get_kernel_time": [H, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                 ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)],
@@ -200,3 +231,111 @@ class Lattice:
         if status != 0 and raise_on_fail:
             _check(status, self._h)
         return SolveResult(x, st.as_dict(), status)
+
+
+def madwf_solve(outer: Lattice, inner: Lattice, m: float, b: torch.Tensor, n_dc=3, tol_pv=1e-8, tol_mob=1e-5,
+                tol_final=1e-10, inner_prec="f32", max_iter=100000, delta=0.1, check_every=10,
+                raise_on_fail=True) -> SolveResult:
+    """Moebius-accelerated solve of D_DW(m) x = b on `outer` through the Moebius
+    lattice `inner` (see include/dwf.h, madwf_solve)."""
+    x = torch.empty_like(b)
+    prm = MadwfParams(int(n_dc), float(tol_pv), float(tol_mob), float(tol_final), _PREC[inner_prec],
+                      int(max_iter), float(delta), int(check_every))
+    st = MadwfStats()
+    with torch.cuda.device(outer.device):
+        status = lib().madwf_solve(outer.handle, inner.handle, float(m), _VP(_ptr(b, outer.spinor_shape)),
+                                   _VP(_ptr(x, outer.spinor_shape)), ctypes.byref(prm), ctypes.byref(st))
+    if status != 0 and raise_on_fail:
+        _check(status, outer.handle)
+    return SolveResult(x, st.as_dict(), status)
+
+
+# --------------------------------------------------------------------------- action, force, integrator
+
+
+def _terms(terms):
+    arr = (Quotient * len(terms))(*[Quotient(float(a), float(b)) for a, b in terms])
+    return arr
+
+
+def _ptr_array(ts, shape):
+    return (_VP * len(ts))(*[_VP(_ptr(t, shape)) if t is not None else _VP() for t in ts])
+
+
+def force(lat: Lattice, terms, phis, want_force=True, want_grad=False, X_io=None, tol=1e-12, inner="f64",
+          max_iter=100000, delta=0.1, check_every=10):
+    """Quotient-action value, force components and/or matrix gradient (see
+    include/dwf.h, dwf_force).  Returns (S, F or None, G or None, stats)."""
+    V = (4,) + tuple(reversed(lat.dims))
+    F = torch.empty(V + (8,), dtype=torch.float64, device=lat.device) if want_force else None
+    G = torch.empty(V + (3, 3), dtype=torch.complex128, device=lat.device) if want_grad else None
+    S = ctypes.c_double()
+    st = Stats()
+    prm = CGParams(float(tol), int(max_iter), _PREC[inner], float(delta), int(check_every))
+    xio = _ptr_array(X_io, lat.spinor_shape) if X_io is not None else None
+    lat._call(lib().dwf_force, len(terms), _terms(terms), _ptr_array(phis, lat.spinor_shape), xio,
+              _VP(_ptr(F, dtype=torch.float64)) if F is not None else _VP(),
+              _VP(_ptr(G)) if G is not None else _VP(), ctypes.byref(S), ctypes.byref(prm), ctypes.byref(st))
+    return S.value, F, G, st.as_dict()
+
+
+def fgi_link_update(lat: Lattice, X: torch.Tensor, coeff: float, U_in: torch.Tensor, U_out=None) -> torch.Tensor:
+    """U_out = exp(coeff * X^j T_j) U_in (Sec. 2 force-gradient update)."""
+    U_out = torch.empty_like(U_in) if U_out is None else U_out
+    lat._call(lib().fgi_link_update, _VP(_ptr(X, dtype=torch.float64)), float(coeff),
+              _VP(_ptr(U_in, lat.gauge_shape)), _VP(_ptr(U_out, lat.gauge_shape)))
+    return U_out
+
+
+def momentum_update(lat: Lattice, F: torch.Tensor, coeff: float, p: torch.Tensor):
+    lat._call(lib().dwf_momentum_update, _VP(_ptr(F, dtype=torch.float64)), float(coeff),
+              _VP(_ptr(p, dtype=torch.float64)))
+
+
+def kinetic(lat: Lattice, p: torch.Tensor) -> float:
+    T = ctypes.c_double()
+    lat._call(lib().dwf_kinetic, _VP(_ptr(p, dtype=torch.float64)), ctypes.byref(T))
+    return T.value
+
+
+def fgi_step(lat: Lattice, terms, phis, U: torch.Tensor, p: torch.Tensor, tau: float, forecast=True, tol=1e-12,
+             inner="f64", max_iter=100000):
+    """One force-gradient PQPQP step, U and p updated in place.  Returns
+    (stats, (iterations of F(U), iterations of F(U')) in the force-gradient step)."""
+    st = Stats()
+    fg = (ctypes.c_int * 2)()
+    prm = CGParams(float(tol), int(max_iter), _PREC[inner], 0.1, 10)
+    lat._call(lib().fgi_step, len(terms), _terms(terms), _ptr_array(phis, lat.spinor_shape),
+              _VP(_ptr(U, lat.gauge_shape)), _VP(_ptr(p, dtype=torch.float64)), float(tau), int(bool(forecast)),
+              ctypes.byref(prm), ctypes.byref(st), fg)
+    return st.as_dict(), (fg[0], fg[1])
+
+
+def hamiltonian(lat: Lattice, terms, phis, U: torch.Tensor, p: torch.Tensor, tol=1e-12) -> float:
+    """H = 1/2 sum (p^j)^2 + S_f (FP64); sets the lattice's gauge field to U."""
+    lat.set_gauge(U)
+    S, _, _, _ = force(lat, terms, phis, want_force=False, tol=tol)
+    return kinetic(lat, p) + S
+
+
+class QuotientAction(torch.autograd.Function):
+    """S(U) for a set of quotient terms; backward returns the library's
+    complex-matrix gradient 2 dS / d conj(U) (torch's convention), computed
+    by the adjoint force kernel."""
+
+    @staticmethod
+    def forward(ctx, U, lat, terms, phis, tol):
+        lat.set_gauge(U.detach())
+        S, _, G, _ = force(lat, terms, phis, want_force=False, want_grad=True, tol=tol)
+        ctx.save_for_backward(G)
+        return torch.tensor(S, dtype=torch.float64, device=U.device)
+
+    @staticmethod
+    def backward(ctx, gS):
+        (G,) = ctx.saved_tensors
+        return gS.to(G.dtype) * G, None, None, None, None
+
+
+def action(lat: Lattice, U: torch.Tensor, terms, phis, tol=1e-12) -> torch.Tensor:
+    """Differentiable quotient action (torch.autograd)."""
+    return QuotientAction.apply(U, lat, terms, phis, tol)

@@ -81,6 +81,21 @@ def test_cg_mobius_matches_oracle(dwf, bc):
     lat.close()
 
 
+@pytest.mark.parametrize("Ls", [5, 12])
+@pytest.mark.parametrize("inner", ["f32", "f16"])
+def test_cg_mixed_ragged_shapes(dwf, Ls, inner):
+    """Odd Ls (a padding slot in the slice-pair layout), Ls = 12 (Lh = 6 pairs,
+    21 sites per CTA) and a ragged last CTA (Vh = 96)."""
+    dims, m = (4, 4, 2, 6), 0.05
+    U = I.gauge_field(9, dims, 0.5)
+    src = I.gaussian_spinor(9, dims, Ls)
+    lat = dwf.Lattice(dims, Ls, M5)
+    lat.set_gauge(_to(U))
+    r = lat.cg(m, _to(src), tol=1e-10, inner=inner)
+    assert _true_res(U, r.x.cpu().numpy(), src, m) <= 1e-10
+    lat.close()
+
+
 def test_zero_source_gives_zero(small, dwf):
     lat, U, b, xo = small
     r = lat.cg(0.04, torch.zeros(lat.spinor_shape, dtype=torch.complex128, device="cuda"))

@@ -202,6 +202,29 @@ dwf_status dwf_kinetic(dwf_lattice_t h, const void* p, double* T);
 dwf_status fgi_step(dwf_lattice_t h, int nterms, const dwf_quotient* terms, const void* const* phi, void* U, void* p,
                     double tau, int forecast, const dwf_cg_params* cg, dwf_stats* stats, int* fg_iters);
 
+/* dwf_apply_Mpc without any device allocation (the paper has no counterpart;
+ * this serves callers that must not allocate while they run: work recorded
+ * into a CUDA graph, code whose allocator owns all device memory, loops that
+ * may not stall on the driver).  Same operator, arguments and boundary
+ * layout as dwf_apply_Mpc.  The handle must already exist (creation and
+ * dwf_set_gauge allocate; this call does not).
+ *
+ * Scratch: one file-scope device array of DWF_NOALLOC_SCRATCH_BYTES bytes,
+ * present on every GPU that loads the library until the process exits.  The
+ * call needs 4 FP64 half-lattice fields (each Vh * 12 * ceil(Ls/2) * 32 bytes,
+ * rounded up to 256); larger lattices are rejected with DWF_ERR_INVALID_ARG
+ * and a message giving both sizes.  Möbius parameters whose fifth-dimension
+ * inverse would need the dense fallback are rejected the same way.
+ * The first call on a device looks up the array's device address there
+ * (cudaGetSymbolAddress, once per device, with that device current); make
+ * that first call before any stream capture.  All calls on a device share
+ * the array and it keeps the last call's contents (every word a call reads
+ * is written earlier in the same call), so calls that overlap on the GPU --
+ * on different streams or handles at the same time -- race.  Kernel timing
+ * (dwf_set_kernel_timing) is suspended during the call. */
+#define DWF_NOALLOC_SCRATCH_BYTES (32u << 20)
+dwf_status dwf_apply_Mpc_noalloc(dwf_lattice_t h, double m, int dag, const void* in, void* out);
+
 /* Instrumentation (no counterpart in the paper; used to measure the Wilson
  * hop kernels against the HBM roofline).  With timing enabled every hop
  * launch on the handle's stream is bracketed by CUDA events.

@@ -87,6 +87,7 @@ def _declare(lib):
         "dwf_apply_Mpc": [H, ctypes.c_double, ctypes.c_int, _VP, _VP],
         "dwf_cg": [H, ctypes.c_double, _VP, _VP, ctypes.POINTER(CGParams), ctypes.POINTER(Stats)],
         "madwf_solve": [H, H, ctypes.c_double, _VP, _VP, ctypes.POINTER(MadwfParams), ctypes.POINTER(MadwfStats)],
+        "dwf_apply_Mpc_noalloc": [H, ctypes.c_double, ctypes.c_int, _VP, _VP],
         "dwf_force": [H, ctypes.c_int, ctypes.POINTER(Quotient), ctypes.POINTER(_VP), ctypes.POINTER(_VP), _VP, _VP,
                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(CGParams), ctypes.POINTER(Stats)],
         "fgi_link_update": [H, _VP, ctypes.c_double, _VP, _VP],
@@ -217,6 +218,14 @@ class Lattice:
     def apply_Mpc(self, m: float, x: torch.Tensor, dag: bool = False, out=None) -> torch.Tensor:
         out = self._new() if out is None else out
         self._call(lib().dwf_apply_Mpc, float(m), int(bool(dag)), _VP(_ptr(x, self.spinor_shape)),
+                   _VP(_ptr(out, self.spinor_shape)))
+        return out
+
+    def apply_Mpc_noalloc(self, m: float, x: torch.Tensor, out: torch.Tensor, dag: bool = False) -> torch.Tensor:
+        """apply_Mpc into a caller-provided `out`; the library allocates no
+        device memory during the call (for callers that must not allocate,
+        e.g. while recording a CUDA graph; see include/dwf.h)."""
+        self._call(lib().dwf_apply_Mpc_noalloc, float(m), int(bool(dag)), _VP(_ptr(x, self.spinor_shape)),
                    _VP(_ptr(out, self.spinor_shape)))
         return out
 

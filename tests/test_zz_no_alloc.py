@@ -1,0 +1,52 @@
+"""The allocation-free entry point dwf_apply_Mpc_noalloc, for callers that
+must not allocate device memory while they run (work recorded into a CUDA
+graph, code whose allocator owns all device memory): it must give the same
+result as dwf_apply_Mpc, on repeated calls that reuse its fixed scratch, and
+refuse lattices larger than that scratch.
+
+This file is collected last on purpose, so that a run stopping at the first
+failure has already run every other test.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_1111_5059_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+M5 = 1.8
+
+
+def _to(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def _rel(a, b):
+    return float((a - b).abs().max() / b.abs().max())
+
+
+@pytest.mark.parametrize("case", [((4, 4, 4, 4), 8, 1.0, 0.0, 1, 0.04), ((4, 2, 4, 6), 12, 1.5, 0.5, -1, 0.01),
+                                  ((8, 8, 8, 8), 16, 11 / 6, 5 / 6, 1, 0.002)])
+def test_noalloc_matches_apply_Mpc_on_repeated_calls(dwf, case):
+    dims, Ls, b, c, bc_t, m = case
+    lat = dwf.Lattice(dims, Ls, M5, b, c, bc_t)
+    lat.set_gauge(_to(I.gauge_field(7, dims, 0.5)))
+    for dag in (False, True):
+        for seed in (1, 2):  # two calls in a row, different inputs
+            x = _to(I.gaussian_spinor(seed, dims, Ls))
+            want = lat.apply_Mpc(m, x, dag=dag)
+            out = torch.full_like(x, complex(float("nan"), 0.0))
+            got = lat.apply_Mpc_noalloc(m, x, out, dag=dag)
+            assert got.data_ptr() == out.data_ptr()
+            assert _rel(got, want) < 1e-13
+    lat.close()
+
+
+def test_noalloc_rejects_lattices_beyond_its_scratch(dwf):
+    lat = dwf.Lattice((16, 16, 16, 16), 16, M5)
+    lat.set_gauge(_to(I.gauge_field(8, (16, 16, 16, 16), 0.5)))
+    x = torch.zeros(lat.spinor_shape, dtype=torch.complex128, device="cuda")
+    with pytest.raises(dwf.DWFError, match="too large for the fixed scratch"):
+        lat.apply_Mpc_noalloc(0.1, x, torch.empty_like(x))
+    lat.close()

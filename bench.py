@@ -11,7 +11,7 @@ achieved HBM bandwidth is reported against the measured copy peak.
 A step is one solve from a zero guess on seeded synthetic inputs already
 resident in HBM (timed with CUDA events on the solve's stream).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload madwf|mixed]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload madwf|mixed|hopprof|ladder]
                   [--impl native|reference] [--no-fp64] [--no-cpu-baseline]
 
 Under torchrun (N > 1) every rank solves its own replica (no collective on
@@ -43,10 +43,18 @@ WORKLOADS = {
     # 16^3 x 32 x Ls=16 Shamir, m_f = 0.01, eps = 0.5: mixed-precision CG
     "mixed": dict(name="shamir-16^3x32-Ls16-mixedCG", dims=(16, 16, 16, 32), Ls=16, M5=1.8, m=0.01, eps=0.5,
                   seed=2, inner="f32", madwf=False, sample_T=4),
+    # the kernel-profiling case: every FP32 half-lattice field (509 MB) is larger than L2
+    "hopprof": dict(name="shamir-24^3x48-Ls16-mixedCG", dims=(24, 24, 24, 48), Ls=16, M5=1.8, m=0.01, eps=0.5,
+                    seed=2, inner="f32", madwf=False, sample_T=2),
+    # Hasenbusch ladder: Moebius 32^3 x 64 x Ls=16 (b = 1.5, c = 0.5), four Gaussian sources at the
+    # masses {0.001, 0.01, 0.05, 0.2}, solved together by the multi-right-hand-side CG
+    "ladder": dict(name="ladder-mobius-32^3x64-Ls16-4rhs", dims=(32, 32, 32, 64), Ls=16, M5=1.8,
+                   masses=(0.001, 0.01, 0.05, 0.2), m=0.001, b5=1.5, c5=0.5, eps=0.6, seed=5, inner="f32",
+                   madwf=False, ladder=True, sample_T=2),
 }
 # FP64 CG iterations to 1e-10 on each input (GB300, dwf_cg inner=f64); they scale the
 # per-iteration oracle time of the reference arm when the FP64 solve is not run.
-FP64_ITERS = {"madwf": 1500, "mixed": 250}
+FP64_ITERS = {"madwf": 300, "mixed": 250, "hopprof": 260, "ladder": 1600}
 
 
 def parse():
@@ -155,6 +163,8 @@ def max_over_ranks(world, v, device):
 
 
 def metric_name(w):
+    if w.get("ladder"):
+        return "DWF solve time @1e-10 (4-mass ladder, multi-RHS mixed CG)"
     return "DWF solve time @1e-10 (" + ("MADWF+mixed" if w["madwf"] else "mixed-precision CG") + ")"
 
 
@@ -166,6 +176,9 @@ def config_of(w, inner):
     if w["madwf"]:
         c.update({"Ls_inner": w["inner_Ls"], "b_inner": w["b"], "c_inner": w["c"], "n_dc": w["n_dc"],
                   "tol_pv": w["tol_pv"], "tol_mob": w["tol_mob"]})
+    if w.get("ladder"):
+        c.update({"m_f": list(w["masses"]), "b": w["b5"], "c": w["c5"], "nrhs": len(w["masses"]),
+                  "sources": f"Gaussian, seeds {w['seed']}..{w['seed'] + len(w['masses']) - 1}"})
     return c
 
 
@@ -185,7 +198,7 @@ def oracle_iteration_seconds(w):
     dims = (X, Y, Z, w["sample_T"])
     U = inputs.gauge_field(w["seed"], dims, w["eps"])
     b = inputs.gaussian_spinor(w["seed"], dims, w["Ls"])
-    eo = O.EO(U, w["m"], w["M5"], w["Ls"])
+    eo = O.EO(U, w["m"], w["M5"], w["Ls"], w.get("b5", 1.0), w.get("c5", 0.0))
     v = b * eo.even
     t0 = time.perf_counter()
     q = eo.Mpc(v)
@@ -198,8 +211,10 @@ def sample_text(w, iters, per_it):
     X, Y, Z, T = w["dims"]
     slab = f"a {X}x{Y}x{Z}x{w['sample_T']} t-slab scaled by {T // w['sample_T']}" if w["sample_T"] < T \
         else "the full lattice"
+    what = "the summed iterations of the FP64 CG solves of the ladder's masses" if w.get("ladder") \
+        else "the iterations of the FP64 CG solve of this input"
     return (f"one FP64 oracle CG iteration (M_pc then M_pc^+) on {slab} ({per_it:.1f} s per full-volume "
-            f"iteration), times the {iters} iterations of the FP64 CG solve of this input")
+            f"iteration), times {iters}, {what}")
 
 
 def run_reference(args, w):
@@ -224,6 +239,124 @@ def run_reference(args, w):
 # --------------------------------------------------------------------------- native arm
 
 
+def run_ladder(args, w, inner, world, rank, local, dev, hbm_peak, peak_src):
+    """The mass ladder: one step is one dwf_cg_multi call over all masses (CUDA
+    graphs on, launch shapes from the autotuner, tuned during warm-up)."""
+    import torch
+
+    from paper_1111_5059_gb300 import dwf, inputs
+
+    masses = w["masses"]
+    n = len(masses)
+    U = torch.from_numpy(inputs.gauge_field(w["seed"], w["dims"], w["eps"])).to(dev)
+    b_host = [torch.from_numpy(inputs.gaussian_spinor(w["seed"] + r, w["dims"], w["Ls"])).pin_memory()
+              for r in range(n)]
+    bs = [h.to(dev) for h in b_host]
+    x_host = [torch.empty_like(h).pin_memory() for h in b_host]
+    stream = torch.cuda.current_stream(dev)
+    lat = dwf.Lattice(w["dims"], w["Ls"], w["M5"], w["b5"], w["c5"], 1, stream=stream, device=dev)
+    lat.set_gauge(U)
+    del U
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def solve(srcs):
+        return lat.cg_multi(masses, srcs, tol=args.tol, inner=inner, delta=0.1, check_every=10)
+
+    tune_s = 0.0
+    for _ in range(args.warmup):
+        _, _, info, _ = solve(bs)
+        tune_s += info["tune_seconds"]
+    torch.cuda.synchronize()
+
+    lat.set_kernel_timing(True)
+    n0 = lat.launch_count()
+    step_ms, infos, stats = [], [], []
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            xs, st, info, _ = solve(bs)
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            infos.append(info)
+            stats.append(st)
+            del xs
+    torch.cuda.synchronize()
+    barrier(world)
+    launches = lat.launch_count() - n0
+    kt = lat.kernel_time(inner)
+    lat.set_kernel_timing(False)
+    total_ms = max_over_ranks(world, sum(step_ms), dev)
+    ms_step = total_ms / args.steps
+    value = ms_step / 1e3 / world
+
+    # ---- e2e: sources from pinned host memory in, solutions back out, inside the timed region
+    e2e = []
+    for _ in range(max(1, min(args.steps, 2))):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        bd = [h.to(dev, non_blocking=True) for h in b_host]
+        xs, _, _, _ = solve(bd)
+        for xh, xd in zip(x_host, xs):
+            xh.copy_(xd, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e.append(e0.elapsed_time(e1))
+        del bd, xs
+    e2e_ms = max_over_ranks(world, statistics.mean(e2e), dev)
+
+    # ---- the same four solves one after the other (single-RHS mixed CG)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    seq = [lat.cg(m, bb, tol=args.tol, inner=inner, delta=0.1, check_every=10) for m, bb in zip(masses, bs)]
+    e1.record(stream)
+    e1.synchronize()
+    seq_s = e0.elapsed_time(e1) / 1e3
+    sequential = {"seconds": seq_s, "iters": [r.stats["iters"] for r in seq],
+                  "true_resid": [r.stats["true_resid"] for r in seq], "speedup_of_headline": seq_s / (ms_step / 1e3)}
+    del seq
+
+    st, info = stats[-1], infos[-1]
+    achieved = kt["bytes"] / (kt["ms"] / 1e3) / 1e9 if kt["ms"] > 0 else None
+    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+            "frac": (achieved / hbm_peak) if achieved else None, "traffic": None,
+            "kernel": f"hop3_kernel<{inner}> batched over right-hand sides (Wilson hop at every s, fused "
+                      "fifth-dimension epilogues per mass)",
+            "launches": kt["launches"], "avg_launch_us": kt["ms"] / max(1, kt["launches"]) * 1e3,
+            "bytes_per_launch": kt["bytes"] / max(1, kt["launches"]),
+            "timed_launches": "the eager first iteration of each batch (graph replays are not bracketed by events)",
+            "peak_source": ("of measured hbm_gbs (MEASURED_PEAKS.json)" if peak_src == "measured"
+                            else "of fallback 6.8 TB/s")}
+    solve_info = {"iters": [s["iters"] for s in st], "reliable_updates": [s["reliable_updates"] for s in st],
+                  "op_count": [s["op_count"] for s in st], "true_resid": [s["true_resid"] for s in st],
+                  "joint_iterations": info["iterations"], "batch": info["batch"], "ctas_per_sm": info["ctas_per_sm"],
+                  "graphs": info["graphs"], "replays": info["replays"], "autotune_seconds_warmup": tune_s,
+                  "step_ms": step_ms}
+    line = {"metric": metric_name(w), "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64" if inner == "f32" else "f16-storage/f32+f64",
+            "data": "synthetic", "config": config_of(w, inner), "roofline": roof,
+            "e2e": {"value": e2e_ms / 1e3 / world, "unit": "s",
+                    "h2d_bytes_per_step": sum(h.numel() * 16 for h in b_host),
+                    "d2h_bytes_per_step": sum(h.numel() * 16 for h in x_host)},
+            "gpu_launches": launches, "solve": solve_info, "sequential_cg": sequential, "clocks": clk.summary()}
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            iters = sum(s["iters"] for s in st)
+            per_it = oracle_iteration_seconds(w)
+            line["cpu_baseline"] = {"value": per_it * iters, "unit": "s", "cores": 1, "kind": "oracle",
+                                    "sample": sample_text(w, iters, per_it)
+                                    + " (the mixed solves' iteration counts stand in for FP64 CG's)"}
+        print(json.dumps(line), flush=True)
+    lat.close()
+
+
 def main():
     args = parse()
     w = WORKLOADS[args.workload]
@@ -243,6 +376,13 @@ def main():
 
         build.build()
     hbm_peak, peak_src = measured_peak()
+    if w.get("ladder"):
+        run_ladder(args, w, inner, world, rank, local, dev, hbm_peak, peak_src)
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.destroy_process_group()
+        return
 
     U = torch.from_numpy(inputs.gauge_field(w["seed"], w["dims"], w["eps"])).to(dev)
     b_host = torch.from_numpy(inputs.gaussian_spinor(w["seed"], w["dims"], w["Ls"])).pin_memory()

@@ -110,6 +110,44 @@ typedef struct {
 dwf_status dwf_cg(dwf_lattice_t h, double m, const void* b, void* x,
                   const dwf_cg_params* params, dwf_stats* stats);
 
+/* Multi-right-hand-side solve for a Hasenbusch mass ladder (Sec. 3: the
+ * determinant ratios over the masses m + mu_i of the splitting put one Dirac
+ * equation per mass on the same gauge field): D(m_r) x_r = b_r for
+ * r = 0 .. nrhs-1, each by the even-odd CG of dwf_cg (same tolerance, inner
+ * precision and FP64 reliable updates, per right-hand side), iterated in
+ * lockstep so that each Wilson hop step of an iteration covers every
+ * unconverged right-hand side in as few launches as the kernel takes (the
+ * links of a 4D site are read once for all of them; each right-hand side's
+ * fifth-dimension operators use its own mass).  Converged right-hand sides
+ * leave the batch.  masses[nrhs] must be distinct; b[nrhs] and x[nrhs] are
+ * host arrays of device pointers to whole-lattice boundary-layout spinors
+ * (x: initial guess in, solution out; no x may alias a b or another x).
+ * stats[nrhs] (may be NULL) receives per-right-hand-side statistics (seconds
+ * and launches are those of the whole call).  opt may be NULL (graphs and
+ * autotuning on).  Work runs on the handle's stream; with graphs on it is
+ * recorded and replayed on a private stream joined to it on both ends.
+ * Returns DWF_ERR_NOT_CONVERGED if some right-hand side hit max_iter (the
+ * others are solved), DWF_ERR_NAN on a non-finite norm. */
+#define DWF_MAX_RHS 16
+typedef struct {
+  int use_graph;  /* 1: record one iteration of a batch as a CUDA graph and replay it */
+  int autotune;   /* 1: pick launch shapes by timing candidates (cached per process,
+                     and in the file named by DWF_TUNE_CACHE if set); 0: defaults */
+} dwf_multi_options;
+typedef struct {
+  int batch;            /* right-hand sides per hop launch for the largest batch */
+  int ctas_per_sm;      /* CTAs per SM for that launch (0: all that fit) */
+  double tune_seconds;  /* time this call spent autotuning */
+  int graphs;           /* CUDA graphs recorded */
+  long long replays;    /* graph launches */
+  int iterations;       /* iterations of the joint loop */
+  double seconds;       /* wall time of the call */
+  long long launches;   /* kernels launched (graph replays count their kernels) */
+} dwf_multi_info;
+dwf_status dwf_cg_multi(dwf_lattice_t h, int nrhs, const double* masses, const void* const* b,
+                        void* const* x, const dwf_cg_params* params, const dwf_multi_options* opt,
+                        dwf_stats* stats, dwf_multi_info* info);
+
 /* Moebius-accelerated DWF solve (Sec. 4, the four-step algorithm with
  * Eqs. trans_5d_4d_source, mob_eq_4d, mob_eq_5d and recon; Sec. 5, defect
  * correction; Table 1).  `outer` is the Shamir lattice (b = 1, c = 0) of

@@ -65,7 +65,7 @@ dwf_status fetch_scalars(dwf_lattice* L) {
   DWF_CUDA(L, cudaMemcpyAsync(L->hscal, L->scal, kScalars * sizeof(double), cudaMemcpyDeviceToHost, L->stream));
   DWF_CUDA(L, cudaStreamSynchronize(L->stream));
   if (L->timing) DWF_TRY(timing_drain(L));
-  return DWF_OK;
+  return check_dev_err(L);
 }
 
 // r64 = b' - M~ x64 (FP64) and |r64|^2 -> hscal[S_TMP0] (synchronises)

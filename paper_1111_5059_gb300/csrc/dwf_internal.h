@@ -24,6 +24,7 @@
 
 #include <cstdint>
 #include <deque>
+#include <functional>
 #include <map>
 #include <string>
 #include <vector>
@@ -279,7 +280,8 @@ struct dwf_lattice {
 namespace dwf {
 
 constexpr int kPartials = 1 << 18;
-constexpr int kScalars = 64;
+constexpr int kScalars = 256;  // [0, 64): single solves; [64, 64 + 8 DWF_MAX_RHS): multi-RHS
+constexpr int kMaxBatch = 8;          // right-hand sides in one hop launch
 
 // error helpers (lattice.cu)
 dwf_status fail(dwf_lattice* L, dwf_status st, const std::string& msg);
@@ -342,6 +344,39 @@ struct HopCall {
   int* nblocks = nullptr;
 };
 dwf_status launch_hop(dwf_lattice* L, const HopCall& c);
+
+// One hop launch over several right-hand sides that share the links: the
+// fields and fifth-dimension operators (one mass each) come from the batch,
+// everything else from c (c.in / c.out / c.x / c.ops / c.partials unused).
+// partials[r] receives right-hand side r's per-block partial sums of |out|^2
+// (kPartials doubles each).  ctas_per_sm = 0: as many as fit.  Needs an
+// FP32 / FP16 shape the pipelined kernel takes (hop_batch_max).
+struct HopBatch {
+  int nrhs = 0;
+  Field in[kMaxBatch], out[kMaxBatch], x[kMaxBatch];
+  const SOps* ops[kMaxBatch] = {};
+  double* partials[kMaxBatch] = {};
+};
+dwf_status launch_hop_batch(dwf_lattice* L, const HopCall& c, const HopBatch& b, int ctas_per_sm);
+// largest batch a single launch takes at this Ls and precision (0: none)
+int hop_batch_max(int Ls, dwf_prec prec);
+
+// tune.cu: launch-shape autotuner for batched hops
+struct HopShape {
+  long Vh;
+  int Ls, prec, nrhs, dag, has_x, ex_kind, eout_kind;
+  std::string key() const;
+};
+struct HopChoice {
+  int batch = 1;        // right-hand sides per launch
+  int ctas_per_sm = 0;  // 0: as many as fit
+  double ms = 0.0;      // measured time of the whole step
+};
+std::vector<HopChoice> hop_candidates(const HopShape& s, int bmax);
+// The cached choice for s, or (first time) the fastest candidate: each is run
+// through `run` (which must launch the whole step on L->stream) and timed.
+dwf_status tune_hop(dwf_lattice* L, const HopShape& s, int bmax, const std::function<dwf_status(const HopChoice&)>& run,
+                    HopChoice* choice, double* tune_seconds);
 
 // s-local: out = a * E x + bcoef * y   (E may be identity), on one parity
 dwf_status launch_sop(dwf_lattice* L, Field x, Field out, const SOps* ops, SOps::Kind e, double a,

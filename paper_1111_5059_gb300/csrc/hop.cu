@@ -27,8 +27,9 @@
 namespace dwf {
 
 // hop2.cu: the slice-pair kernel with bulk-copy staging for FP32 / FP16 storage
-int hop2_sites(int Ls, int prec);
-dwf_status launch_hop2(dwf_lattice* L, const HopCall& c, const SOpK<float>& ex, const SOpK<float>& eout, int NS);
+int hop2_sites(int Ls, int prec, int nr);
+dwf_status launch_hop2(dwf_lattice* L, const HopCall& c, const HopBatch& b, const SOpK<float>* ex,
+                       const SOpK<float>* eout, int G, int ctas_per_sm);
 
 // ---------------------------------------------------------------- hop kernel
 
@@ -227,9 +228,17 @@ static dwf_status hop_t(dwf_lattice* L, const HopCall& c) {
   cudaEvent_t ta = nullptr, tb = nullptr;
   if (L->timing) DWF_TRY(timing_begin(L, &ta, &tb));
   int NS2 = 0;
-  if constexpr (sizeof(S) <= 4) NS2 = hop2_sites(L->Ls, pi);
+  if constexpr (sizeof(S) <= 4) NS2 = hop2_sites(L->Ls, pi, 1);
   if (NS2 > 0) {
-    if constexpr (sizeof(S) <= 4) DWF_TRY(launch_hop2(L, c, a.ex, a.eout, NS2));
+    if constexpr (sizeof(S) <= 4) {
+      HopBatch b;
+      b.nrhs = 1;
+      b.in[0] = c.in;
+      b.out[0] = c.out;
+      b.x[0] = c.x;
+      b.partials[0] = c.partials;
+      DWF_TRY(launch_hop2(L, c, b, &a.ex, &a.eout, NS2, 0));
+    }
   } else if (c.dag) {
     if (smem > 48 * 1024)
       DWF_CUDA(L, cudaFuncSetAttribute(hop_kernel<S, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -263,6 +272,45 @@ dwf_status launch_hop(dwf_lattice* L, const HopCall& c) {
     case DWF_F16: return hop_t<__half>(L, c);
   }
   return fail(L, DWF_ERR_INVALID_ARG, "hop: bad precision");
+}
+
+int hop_batch_max(int Ls, dwf_prec prec) {
+  for (int n = kMaxBatch; n >= 1; --n)
+    if (hop2_sites(Ls, prec, n) > 0) return n;
+  return 0;
+}
+
+dwf_status launch_hop_batch(dwf_lattice* L, const HopCall& c, const HopBatch& b, int ctas_per_sm) {
+  if (!L->gauge_set) return fail(L, DWF_ERR_INVALID_ARG, "gauge field not set");
+  const int nr = b.nrhs;
+  if (nr < 1 || nr > kMaxBatch) return fail(L, DWF_ERR_INVALID_ARG, "hop batch: bad number of right-hand sides");
+  const dwf_prec pi = b.in[0].prec;
+  const int G = hop2_sites(L->Ls, pi, nr);
+  if (G < 1) return fail(L, DWF_ERR_INVALID_ARG, "hop batch: shape not supported by the pipelined kernel");
+  SOpK<float> ex[kMaxBatch], eout[kMaxBatch];
+  for (int r = 0; r < nr; ++r) {
+    if (b.in[r].prec != pi || b.out[r].prec != pi || (c.has_x && b.x[r].prec != pi) || !b.ops[r])
+      return fail(L, DWF_ERR_INVALID_ARG, "hop batch: mixed precisions or missing operators");
+    if ((b.partials[r] != nullptr) != (b.partials[0] != nullptr))
+      return fail(L, DWF_ERR_INVALID_ARG, "hop batch: partial sums for some right-hand sides only");
+    ex[r] = sop_k<float>(c.has_x ? b.ops[r] : nullptr, c.ex, L->Ls);
+    eout[r] = sop_k<float>(b.ops[r], c.eout, L->Ls);
+    if (ex[r].kind != ex[0].kind || eout[r].kind != eout[0].kind)
+      return fail(L, DWF_ERR_INVALID_ARG, "hop batch: operator kinds differ between masses");
+  }
+  cudaEvent_t ta = nullptr, tb = nullptr;
+  if (L->timing) DWF_TRY(timing_begin(L, &ta, &tb));
+  DWF_TRY(launch_hop2(L, c, b, ex, eout, G, ctas_per_sm));
+  counted(L);
+  if (L->timing) {
+    const double w = pi == DWF_F32 ? 4.0 : 2.0;
+    const double spin = 24.0 * w + (pi == DWF_F16 ? 4.0 : 0.0);
+    const double sites = (double)L->Vh * L->Ls * nr;
+    const double bytes = sites * spin * (c.has_x ? 3.0 : 2.0) + (double)L->Vh * 8 * 18 * w;
+    timing_end(L, pi, bytes, ta, tb);
+  }
+  DWF_CUDA(L, cudaGetLastError());
+  return DWF_OK;
 }
 
 template <class S>

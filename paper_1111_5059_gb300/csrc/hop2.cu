@@ -8,20 +8,25 @@
 // with the fifth-dimension operators of the even-odd Schur form fused).
 //
 // GB300 design:
-//  * A CTA owns NS 4D sites; thread (i, j) owns the slice pair (j, j + Lh) of
-//    site i, so both lanes of every packed FP32x2 FMA (__ffma2_rn) use the
-//    same link element and the arithmetic instruction count halves.
-//  * A neighbour site's whole 5D spinor block is contiguous in the pair
-//    layout, so each direction's NS neighbour blocks are fetched by the bulk
-//    copy engine (cp.async.bulk, completion counted on an mbarrier) into a
-//    two-slot shared-memory ring: direction d + 2 streams in while d is
-//    computed, independently of occupancy.
-//  * The 8 links of each site are read once per CTA into shared memory,
-//    duplicated as (u, u) pairs so they feed the packed FMAs directly, and
-//    reused over all Ls slices.
+//  * Thread (i, j) owns the slice pair (j, j + Lh) of 4D site i, so both
+//    lanes of every packed FP32x2 FMA (__ffma2_rn) use the same link element.
+//  * A CTA is one warp that walks a stream of site groups (G = 32 / Lh sites
+//    per group).  A group is a sequence of stages: the 8 directions (the G
+//    neighbour blocks of that direction -- a neighbour's 5D spinor block is
+//    contiguous in the pair layout; stage 0 also brings the group's links)
+//    and, if the hop has a site term, the group's own block.  Stages are
+//    fetched by the bulk copy engine (cp.async.bulk, completion counted on an
+//    mbarrier per slot) into a ring of kSlots shared-memory slots in issue
+//    order, so kSlots - 1 stages are in flight while one is computed, across
+//    group boundaries, independently of occupancy; no block barrier exists.
+//  * Links are read once per group from shared memory and reused over all Ls
+//    slices; the s-op tile of the epilogue reuses the slot just consumed.
 //  * Waits on the mbarriers are bounded: a wait that gives up sets the
 //    handle's device error flag (reported as DWF_ERR_TIMEOUT), waits once more
-//    for the CTA's own copies and skips the store.
+//    for the warp's own copies and skips the store.
+#include <map>
+#include <mutex>
+
 #include "dwf_internal.h"
 
 #include "hop_common.cuh"
@@ -30,8 +35,8 @@ namespace dwf {
 
 namespace {
 
-constexpr int kThreads2 = 128;
 constexpr long kWaitLimit = 1L << 22;
+constexpr int kSlots = 3;
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) {
   return static_cast<unsigned>(__cvta_generic_to_shared(p));
@@ -104,10 +109,9 @@ __device__ __forceinline__ void cacc(float2& ar, float2& ai, float2 gr, float2 g
 }
 
 // acc += (1 - SG g_MU) U psi on a slice pair; psi given by (pr, pi)[12],
-// link from shared memory as 9 complex (ur, ur, ui, ui) float4.
+// link U as 9 complex (ur, ui), broadcast to both lanes.
 template <int MU, int SG>
-__device__ __forceinline__ void hop_dir2(const float2* pr, const float2* pi, const float4* __restrict__ U,
-                                         float2* ar, float2* ai) {
+__device__ __forceinline__ void hop_dir2(const float2* pr, const float2* pi, const float2* U, float2* ar, float2* ai) {
   typedef Proj<MU, SG> P;
   float2 hr[6], hi[6];
 #pragma unroll
@@ -117,56 +121,39 @@ __device__ __forceinline__ void hop_dir2(const float2* pr, const float2* pi, con
   }
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    float4 u[3];
+    float2 ur[3], ui[3];
 #pragma unroll
-    for (int b = 0; b < 3; ++b) u[b] = U[3 * a + b];
+    for (int b = 0; b < 3; ++b) {
+      ur[b] = f2(U[3 * a + b].x);
+      ui[b] = f2(U[3 * a + b].y);
+    }
 #pragma unroll
     for (int hh = 0; hh < 2; ++hh) {
       // g = sum_b U_ab h_b :  gr = sum ur hr - sum ui hi,  gi = sum ur hi + ui hr
       float2 A = make_float2(0.f, 0.f), B = A, gi = A;
 #pragma unroll
       for (int b = 0; b < 3; ++b) {
-        const float2 ur = make_float2(u[b].x, u[b].y), ui = make_float2(u[b].z, u[b].w);
-        A = fma2(ur, hr[3 * hh + b], A);
-        B = fma2(ui, hi[3 * hh + b], B);
-        gi = fma2(ur, hi[3 * hh + b], gi);
-        gi = fma2(ui, hr[3 * hh + b], gi);
+        A = fma2(ur[b], hr[3 * hh + b], A);
+        B = fma2(ui[b], hi[3 * hh + b], B);
+        gi = fma2(ur[b], hi[3 * hh + b], gi);
+        gi = fma2(ui[b], hr[3 * hh + b], gi);
       }
       const float2 gr = sub2(A, B);
-      // upper spins 0, 1
-      ar[3 * hh + a] = add2(ar[3 * hh + a], gr);
+      ar[3 * hh + a] = add2(ar[3 * hh + a], gr);  // upper spins 0, 1
       ai[3 * hh + a] = add2(ai[3 * hh + a], gi);
-      // lower spins 2, 3
-      if (hh == P::S2) cacc<P::D2R, P::D2I>(ar[6 + a], ai[6 + a], gr, gi);
+      if (hh == P::S2) cacc<P::D2R, P::D2I>(ar[6 + a], ai[6 + a], gr, gi);  // lower spins 2, 3
       if (hh == P::S3) cacc<P::D3R, P::D3I>(ar[9 + a], ai[9 + a], gr, gi);
     }
   }
 }
 
-template <class S> struct Hop2Args {
-  CFieldRef<S> in;
-  FieldRef<S> out;
-  CFieldRef<S> x;
-  const S* links;  // [Vh][8][18]
-  const int* nbr;  // [8][Vh]
-  long Vh;
-  int Ls, Lh, NS;
-  int ring_bytes;  // the ring region (also the s-op tile after the direction loop)
-  SOpK<float> ex, eout;
-  float scale, xscale;
-  double* partials;
-  int* err;
-};
-
-// bytes of one site's spinor block and of its FP16 scales
+// bytes of one complex-component chunk of a slice pair
 template <class S> __host__ __device__ constexpr int chunk_bytes() { return sizeof(S) == 4 ? 16 : 8; }
 
-template <class S> struct Ring;  // per-slot view helpers
-
-// Write the pair (re, im) of slices j, j + Lh of site i into the s-op tile.
-__device__ __forceinline__ void tile_put_pair(float* tile, int R, int i, int j, int Lh, int Ls, const float2* re,
+// Write the pair (re, im) of slices j, j + Lh of tile block bi into the s-op tile.
+__device__ __forceinline__ void tile_put_pair(float* tile, int R, int bi, int j, int Lh, int Ls, const float2* re,
                                               const float2* im) {
-  float* base = tile + (i * 12) * R;
+  float* base = tile + (bi * 12) * R;
   const bool two = j + Lh < Ls;
 #pragma unroll
   for (int k = 0; k < 12; ++k) {
@@ -174,9 +161,9 @@ __device__ __forceinline__ void tile_put_pair(float* tile, int R, int i, int j, 
     if (two) reinterpret_cast<float2*>(base + k * R)[j + Lh] = make_float2(re[k].y, im[k].y);
   }
 }
-__device__ __forceinline__ void tile_get_pair(const float* tile, int R, int i, int j, int Lh, int Ls, float2* re,
+__device__ __forceinline__ void tile_get_pair(const float* tile, int R, int bi, int j, int Lh, int Ls, float2* re,
                                               float2* im) {
-  const float* base = tile + (i * 12) * R;
+  const float* base = tile + (bi * 12) * R;
   const bool two = j + Lh < Ls;
 #pragma unroll
   for (int k = 0; k < 12; ++k) {
@@ -187,19 +174,35 @@ __device__ __forceinline__ void tile_get_pair(const float* tile, int R, int i, i
   }
 }
 
-// (re, im) <- op (re, im) across the CTA, through the tile (all threads call).
-__device__ __forceinline__ void sop_pair(const SOpK<float>& op, float2* re, float2* im, float* tile, int i, int j,
-                                         bool act, int nact, int Ls, int Lh) {
+// arr[r] for a runtime r < kMaxBatch, by selects (arr lives in kernel parameter space)
+template <class T> __device__ __forceinline__ T pick(const T* arr, int r) {
+  T v = arr[0];
+#pragma unroll
+  for (int q = 1; q < kMaxBatch; ++q)
+    if (r == q) v = arr[q];
+  return v;
+}
+
+// (re, im) <- ops[r] (re, im) across the warp, through the tile (all lanes
+// call).  Tile block bi = r * G + i holds site i of right-hand side r; all
+// right-hand sides of a launch share the operator kind.
+template <int NRC>
+__device__ __forceinline__ void sop_pair(const SOpK<float>* ops, float2* re, float2* im, float* tile, int bi, int r,
+                                         int j, bool act, int G, int nact, int nr, int Ls, int Lh) {
   const int R = tile_row(Ls);
-  if (act) tile_put_pair(tile, R, i, j, Lh, Ls, re, im);
-  __syncthreads();
-  if (op.kind == 1) {
-    sop_rows(op, tile, nact, Ls, R);
-    __syncthreads();
-    if (act) tile_get_pair(tile, R, i, j, Lh, Ls, re, im);
+  if (act) tile_put_pair(tile, R, bi, j, Lh, Ls, re, im);
+  __syncwarp();
+  if (ops[0].kind == 1) {
+    for (int w = threadIdx.x; w < nr * G * 12; w += 32) {
+      const int b = w / 12, rr = NRC == 1 ? 0 : b / G;
+      if (b - rr * G < nact) sop_row(pick(ops, rr), tile + w * R, w % 12, Ls);
+    }
+    __syncwarp();
+    if (act) tile_get_pair(tile, R, bi, j, Lh, Ls, re, im);
   } else if (act) {
     // dense fallback: row s of the (already transposed where needed) matrix
-    const float* base = tile + (i * 12) * R;
+    const SOpK<float> op = pick(ops, NRC == 1 ? 0 : r);
+    const float* base = tile + (bi * 12) * R;
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
       re[k] = make_float2(0.f, 0.f);
@@ -224,60 +227,49 @@ __device__ __forceinline__ void sop_pair(const SOpK<float>& op, float2* re, floa
         im[k].y = 0.f;
       }
   }
-  __syncthreads();
-}
-
-__device__ __forceinline__ void unpack_chunk(const float4& a, float2& r, float2& i) {
-  r = make_float2(a.x, a.y);
-  i = make_float2(a.z, a.w);
+  __syncwarp();
 }
 
 // ---------------------------------------------------------------- the pipelined kernel
-//
-// One CTA = one warp.  The warp walks site groups g = blockIdx.x, blockIdx.x +
-// gridDim.x, ...; a group is G = 32 / Lh sites, thread (i, j) owning slice pair
-// j of site i.  Each group is a sequence of stages: directions d = 0..7 (the G
-// neighbour blocks of that direction; stage 0 also brings the group's links)
-// and, if the hop has a site term, the group's own x block.  Stages stream
-// through a two-slot ring in issue order, so the stages of the next group are
-// in flight while this group finishes; the s-op tile of the epilogue reuses
-// the slot of the stage just consumed.
 
-// expanded links: 72 float4 per site, padded so consecutive sites start in different banks
-constexpr int kDupStride = 74;
-
-struct Ctx {  // per-CTA shared-memory layout (byte offsets)
-  int slot_bytes, raw_off, dup_off, total;
+struct Ctx {        // per-CTA shared-memory layout (byte offsets)
+  int slot_bytes;   // one ring slot: G x nr site blocks (+ FP16 scales), or the s-op tile
+  int raw_off;      // two link buffers (groups alternate), one padded block per site
+  int link_stride;  // bytes between two sites' link blocks
+  int total;
 };
 
-__host__ __device__ inline Ctx make_ctx(int Ls, int prec, int G) {
+__host__ __device__ inline Ctx make_ctx(int Ls, int prec, int G, int nr) {
   const int Lh = (Ls + 1) / 2;
   const int cb = prec == DWF_F32 ? 16 : 8;
-  int blocks = G * 12 * Lh * cb + (prec == DWF_F16 ? G * Lh * 8 : 0);
-  const int tile = G * 12 * tile_row(Ls) * 4;
+  const int nb = G * nr;
+  const int blocks = nb * 12 * Lh * cb + (prec == DWF_F16 ? nb * Lh * 8 : 0);
+  const int tile = nb * 12 * tile_row(Ls) * 4;
   int slot = blocks > tile ? blocks : tile;
   slot = (slot + 127) / 128 * 128;
   Ctx c;
   c.slot_bytes = slot;
-  c.raw_off = 2 * slot;
-  c.dup_off = c.raw_off + (G * 8 * 18 * 4 + 127) / 128 * 128;
-  c.total = c.dup_off + G * kDupStride * 16;
+  c.raw_off = kSlots * slot;
+  // 8 links x 18 reals per site, +16 bytes so consecutive sites start in different banks
+  c.link_stride = 8 * 18 * (prec == DWF_F32 ? 4 : 2) + 16;
+  c.total = c.raw_off + 2 * G * c.link_stride;
   return c;
 }
 
+// One launch over nr right-hand sides that share the links (nr = 1: a single field).
 template <class S> struct Hop3Args {
-  CFieldRef<S> in;
-  FieldRef<S> out;
-  CFieldRef<S> x;
-  const S* links;  // [Vh][8][18]
-  const int* nbr;  // [8][Vh]
+  CFieldRef<S> in[kMaxBatch];
+  FieldRef<S> out[kMaxBatch];
+  CFieldRef<S> x[kMaxBatch];
+  SOpK<float> ex[kMaxBatch], eout[kMaxBatch];
+  double* partials[kMaxBatch];  // per right-hand side, one double per CTA (or null)
+  const S* links;               // [Vh][8][18]
+  const int* nbr;               // [8][Vh]
   long Vh;
   long ngroups;
-  int Ls, Lh, G;
+  int Ls, Lh, G, nr;
   Ctx ctx;
-  SOpK<float> ex, eout;
   float scale, xscale;
-  double* partials;
   int* err;
 };
 
@@ -285,12 +277,17 @@ template <class S> struct Pipe {
   const Hop3Args<S>* a;
   unsigned char* sm;
   unsigned bar0;
-  int nstage;  // stages per group
   int blk, sblk;
+  int nr;                         // right-hand sides of the launch
+  const unsigned char* src_in;    // this lane's copy source: in[lane / G] (lane < G nr)
+  const unsigned char* src_in_n;  // its FP16 scales
+  const unsigned char* src_x;     // x[lane] (lane < nr)
+  const unsigned char* src_x_n;
 };
 
-// Issue stage k (0 .. nstage-1) of group g into ring slot `slot`; nb holds
-// the group's neighbour index for direction k (per lane < nact).
+// Issue stage k of group g into ring slot `slot` (all lanes call).  Slot
+// block t = r * G + i holds site i of right-hand side r and is fetched by
+// lane t; nb_k is the neighbour index of that site for direction k (k < 8).
 template <class S>
 __device__ __forceinline__ void issue_stage(const Pipe<S>& P, long g, int k, int slot, int nb_k) {
   const Hop3Args<S>& a = *P.a;
@@ -302,45 +299,48 @@ __device__ __forceinline__ void issue_stage(const Pipe<S>& P, long g, int k, int
   const unsigned bar = P.bar0 + 8u * slot;
   unsigned char* dst = P.sm + slot * a.ctx.slot_bytes;
   const bool fp16 = sizeof(S) == 2;
+  const int lbytes = 8 * 18 * (int)sizeof(S);
+  const int nb = a.G * P.nr;
+  // earlier generic-proxy reads of this slot must be ordered before the copies
   fence_async_smem();
-  unsigned bytes;
-  if (k < 8) {
-    bytes = nact * (P.blk + (fp16 ? P.sblk : 0)) + (k == 0 ? nact * 8 * 18 * (int)sizeof(S) : 0);
-  } else {
-    bytes = nact * (P.blk + (fp16 ? P.sblk : 0));
-  }
+  const unsigned bytes = nact * P.nr * (P.blk + (fp16 ? P.sblk : 0)) + (k == 0 ? nact * lbytes : 0);
   if (lane == 0) mbar_expect_tx(bar, bytes);
   __syncwarp();
   if (k < 8) {
-    if (lane < nact) {
-      bulk_g2s(smem_addr(dst + lane * P.blk), reinterpret_cast<const unsigned char*>(a.in.v) + (long)nb_k * P.blk,
-               P.blk, bar);
-      if (fp16)
-        bulk_g2s(smem_addr(dst + a.G * P.blk + lane * P.sblk),
-                 reinterpret_cast<const unsigned char*>(a.in.norm) + (long)nb_k * P.sblk, P.sblk, bar);
+    if (lane < nb && lane % a.G < nact) {
+      bulk_g2s(smem_addr(dst + lane * P.blk), P.src_in + (long)nb_k * P.blk, P.blk, bar);
+      if (fp16) bulk_g2s(smem_addr(dst + nb * P.blk + lane * P.sblk), P.src_in_n + (long)nb_k * P.sblk, P.sblk, bar);
     }
-    if (k == 0 && lane == 0)
-      bulk_g2s(smem_addr(P.sm + a.ctx.raw_off), a.links + h0 * 8 * 18, nact * 8 * 18 * (int)sizeof(S), bar);
-  } else if (lane == 0) {
-    bulk_g2s(smem_addr(dst), reinterpret_cast<const unsigned char*>(a.x.v) + h0 * P.blk, nact * P.blk, bar);
+    if (k == 0 && lane < nact) {
+      // the links of consecutive groups of this CTA alternate between two
+      // buffers: this copy is issued while the previous group still reads its own
+      const int lb = (int)(((g - blockIdx.x) / gridDim.x) & 1);
+      bulk_g2s(smem_addr(P.sm + a.ctx.raw_off + (lb * a.G + lane) * a.ctx.link_stride),
+               a.links + (h0 + lane) * 8 * 18, lbytes, bar);
+    }
+  } else if (lane < P.nr) {
+    bulk_g2s(smem_addr(dst + lane * a.G * P.blk), P.src_x + h0 * P.blk, nact * P.blk, bar);
     if (fp16)
-      bulk_g2s(smem_addr(dst + a.G * P.blk), reinterpret_cast<const unsigned char*>(a.x.norm) + h0 * P.sblk,
-               nact * P.sblk, bar);
+      bulk_g2s(smem_addr(dst + nb * P.blk + lane * a.G * P.sblk), P.src_x_n + h0 * P.sblk, nact * P.sblk, bar);
   }
 }
 
-// (re, im) of pair j of site i from a slot holding G site blocks
+// (re, im) of pair j of slot block bi
 template <class S>
-__device__ __forceinline__ void read_pair(const Pipe<S>& P, const unsigned char* slot, int i, int j, float2* re,
+__device__ __forceinline__ void read_pair(const Pipe<S>& P, const unsigned char* slot, int bi, int j, float2* re,
                                           float2* im) {
   const int Lh = P.a->Lh;
   if constexpr (sizeof(S) == 4) {
-    const float4* c4 = reinterpret_cast<const float4*>(slot + i * P.blk);
+    const float4* c4 = reinterpret_cast<const float4*>(slot + bi * P.blk);
 #pragma unroll
-    for (int k = 0; k < 12; ++k) unpack_chunk(c4[k * Lh + j], re[k], im[k]);
+    for (int k = 0; k < 12; ++k) {
+      const float4 v = c4[k * Lh + j];
+      re[k] = make_float2(v.x, v.y);
+      im[k] = make_float2(v.z, v.w);
+    }
   } else {
-    const uint2* c2 = reinterpret_cast<const uint2*>(slot + i * P.blk);
-    const float2 sc = reinterpret_cast<const float2*>(slot + P.a->G * P.blk + i * P.sblk)[j];
+    const uint2* c2 = reinterpret_cast<const uint2*>(slot + bi * P.blk);
+    const float2 sc = reinterpret_cast<const float2*>(slot + P.a->G * P.nr * P.blk + bi * P.sblk)[j];
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
       const uint2 v = c2[k * Lh + j];
@@ -352,36 +352,65 @@ __device__ __forceinline__ void read_pair(const Pipe<S>& P, const unsigned char*
   }
 }
 
-template <class S, int DAG, int HX>
-__global__ void __launch_bounds__(32, 11) hop3_kernel(const Hop3Args<S> a) {
+// links of site i, direction d, from link buffer lb, as 9 complex (ur, ui) in FP32
+template <class S>
+__device__ __forceinline__ void site_links(const Pipe<S>& P, int lb, int i, int d, float2* U) {
+  const unsigned char* base = P.sm + P.a->ctx.raw_off + (lb * P.a->G + i) * P.a->ctx.link_stride;
+  if constexpr (sizeof(S) == 4) {
+    const float2* u = reinterpret_cast<const float2*>(base) + d * 9;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) U[e] = u[e];
+  } else {
+    const __half2* u = reinterpret_cast<const __half2*>(base) + d * 9;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) U[e] = __half22float2(u[e]);
+  }
+}
+
+// Lane (i, r, j) = lane / (nr Lh), ... owns slice pair j of site i of
+// right-hand side r; a group is G consecutive sites of all nr right-hand sides.
+template <class S, int DAG, int HX, int NRC>
+__global__ void __launch_bounds__(32, 8) hop3_kernel(const Hop3Args<S> a) {
   extern __shared__ __align__(128) unsigned char sm[];
-  __shared__ __align__(8) unsigned long long bars[2];
-  const int Lh = a.Lh, G = a.G, Ls = a.Ls;
+  __shared__ __align__(8) unsigned long long bars[kSlots];
+  __shared__ double red[32];
+  constexpr int NST = HX ? 9 : 8;  // stages per group
+  const int Lh = a.Lh, G = a.G, Ls = a.Ls, nr = NRC ? NRC : a.nr;
   const int lane = threadIdx.x;
-  const int i = lane / Lh;
-  const int j = lane - i * Lh;
+  const int NJ = nr * Lh;
+  const int i = lane / NJ;
+  const int r = NRC == 1 ? 0 : (lane - i * NJ) / Lh;
+  const int j = lane - i * NJ - r * Lh;
+  const int bi = r * G + i;  // this lane's block in a slot or the tile
   Pipe<S> P;
   P.a = &a;
   P.sm = sm;
   P.bar0 = smem_addr(&bars[0]);
-  P.nstage = HX ? 9 : 8;
   P.blk = 12 * Lh * chunk_bytes<S>();
   P.sblk = Lh * 8;
-  const float4* dup = reinterpret_cast<const float4*>(sm + a.ctx.dup_off);
+  P.nr = nr;
+  {
+    const int rc = (NRC == 1 || lane >= G * nr) ? 0 : lane / G;
+    const CFieldRef<S> fin = pick(a.in, rc);
+    P.src_in = reinterpret_cast<const unsigned char*>(fin.v);
+    P.src_in_n = reinterpret_cast<const unsigned char*>(fin.norm);
+    const CFieldRef<S> fx = pick(a.x, (NRC == 1 || lane >= nr) ? 0 : lane);
+    P.src_x = reinterpret_cast<const unsigned char*>(fx.v);
+    P.src_x_n = reinterpret_cast<const unsigned char*>(fx.norm);
+  }
   if (lane == 0) {
-    mbar_init(P.bar0, 1);
-    mbar_init(P.bar0 + 8, 1);
+    for (int s = 0; s < kSlots; ++s) mbar_init(P.bar0 + 8u * s, 1);
     fence_async_smem();
   }
   __syncwarp();
   const long stride = gridDim.x;
-  // neighbour indices of the current and the next group (lane = site)
+  // neighbour indices of the current and the next group for this lane's copy site
   int nb_cur[8], nb_next[8];
   auto load_nb = [&](long g, int* nb) {
 #pragma unroll
     for (int d = 0; d < 8; ++d) nb[d] = 0;
-    if (g < a.ngroups && lane < G) {
-      const long hh = g * G + lane;
+    if (g < a.ngroups && lane < G * nr) {
+      const long hh = g * G + lane % G;
       if (hh < a.Vh) {
 #pragma unroll
         for (int d = 0; d < 8; ++d) nb[d] = __ldg(a.nbr + (long)d * a.Vh + hh);
@@ -390,9 +419,9 @@ __global__ void __launch_bounds__(32, 11) hop3_kernel(const Hop3Args<S> a) {
   };
   long g = blockIdx.x;
   load_nb(g, nb_cur);
-  issue_stage<S>(P, g, 0, 0, nb_cur[0]);
-  issue_stage<S>(P, g, 1, 1, nb_cur[1]);
-  unsigned seq = 0;  // index of the stage being consumed
+#pragma unroll
+  for (int s = 0; s < kSlots; ++s) issue_stage<S>(P, g, s, s, nb_cur[s]);
+  unsigned seq = 0;  // global index of the stage being consumed; slot seq % kSlots
   bool bad = false;
   double part = 0.0;
   for (; g < a.ngroups; g += stride) {
@@ -401,6 +430,7 @@ __global__ void __launch_bounds__(32, 11) hop3_kernel(const Hop3Args<S> a) {
     const long left = a.Vh - h0;
     const int nact = left < G ? (int)left : G;
     const bool act = i < nact;
+    const int lb = (int)(((g - blockIdx.x) / stride) & 1);
     float2 ar[12], ai[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
@@ -409,32 +439,12 @@ __global__ void __launch_bounds__(32, 11) hop3_kernel(const Hop3Args<S> a) {
     }
 #pragma unroll
     for (int d = 0; d < 8; ++d) {
-      const int slot = seq & 1;
-      if (!mbar_wait(P.bar0 + 8u * slot, (seq >> 1) & 1)) bad = true;
-      const unsigned char* sl = sm + slot * a.ctx.slot_bytes;
-      if (d == 0) {
-        // expand this group's links to (ur, ur, ui, ui)
-        const S* raw = reinterpret_cast<const S*>(sm + a.ctx.raw_off);
-        float4* dw = reinterpret_cast<float4*>(sm + a.ctx.dup_off);
-        for (int q = lane; q < nact * 72; q += 32) {
-          float ur, ui;
-          if constexpr (sizeof(S) == 4) {
-            const float2 v = reinterpret_cast<const float2*>(raw)[q];
-            ur = v.x;
-            ui = v.y;
-          } else {
-            const float2 v = __half22float2(reinterpret_cast<const __half2*>(raw)[q]);
-            ur = v.x;
-            ui = v.y;
-          }
-          dw[(q / 72) * kDupStride + q % 72] = make_float4(ur, ur, ui, ui);
-        }
-        __syncwarp();
-      }
+      const int slot = seq % kSlots;
+      if (!mbar_wait(P.bar0 + 8u * slot, (seq / kSlots) & 1)) bad = true;
       if (act) {
-        float2 pr[12], pi[12];
-        read_pair<S>(P, sl, i, j, pr, pi);
-        const float4* U = dup + i * kDupStride + d * 9;
+        float2 pr[12], pi[12], U[9];
+        read_pair<S>(P, sm + slot * a.ctx.slot_bytes, bi, j, pr, pi);
+        site_links<S>(P, lb, i, d, U);
         constexpr int F = DAG ? -1 : 1;
         if (d == 0) hop_dir2<0, F>(pr, pi, U, ar, ai);
         if (d == 1) hop_dir2<1, F>(pr, pi, U, ar, ai);
@@ -446,10 +456,10 @@ __global__ void __launch_bounds__(32, 11) hop3_kernel(const Hop3Args<S> a) {
         if (d == 7) hop_dir2<3, -F>(pr, pi, U, ar, ai);
       }
       __syncwarp();
-      // refill this slot with the stage two ahead (unless this was the group's last stage)
-      constexpr int NST = HX ? 9 : 8;
-      if (!(NST == 8 && d == 7)) {
-        const int k2 = d + 2;
+      // refill this slot with the stage kSlots ahead; after the group's last
+      // stage the slot first serves as the epilogue's tile
+      if (d != NST - 1) {
+        const int k2 = d + kSlots;
         if (k2 < NST)
           issue_stage<S>(P, g, k2, slot, nb_cur[k2 < 8 ? k2 : 0]);
         else
@@ -464,29 +474,30 @@ __global__ void __launch_bounds__(32, 11) hop3_kernel(const Hop3Args<S> a) {
       ar[k] = make_float2(ar[k].x * sc, ar[k].y * sc);
       ai[k] = make_float2(ai[k].x * sc, ai[k].y * sc);
     }
-    const int last_slot = (seq - 1) & 1;
+    int tslot;
     if (HX) {
-      const int slot = seq & 1;
-      if (!mbar_wait(P.bar0 + 8u * slot, (seq >> 1) & 1)) bad = true;
+      tslot = seq % kSlots;
+      if (!mbar_wait(P.bar0 + 8u * tslot, (seq / kSlots) & 1)) bad = true;
       float2 xr[12], xi[12];
-      if (act) read_pair<S>(P, sm + slot * a.ctx.slot_bytes, i, j, xr, xi);
+      if (act) read_pair<S>(P, sm + tslot * a.ctx.slot_bytes, bi, j, xr, xi);
       __syncwarp();
-      float* tile = reinterpret_cast<float*>(sm + slot * a.ctx.slot_bytes);
-      if (a.ex.kind != 0) sop_pair(a.ex, xr, xi, tile, i, j, act, nact, Ls, Lh);
+      float* tile = reinterpret_cast<float*>(sm + tslot * a.ctx.slot_bytes);
+      if (a.ex[0].kind != 0) sop_pair<NRC>(a.ex, xr, xi, tile, bi, r, j, act, G, nact, nr, Ls, Lh);
       const float2 xs = f2(a.xscale);
 #pragma unroll
       for (int k = 0; k < 12; ++k) {
         ar[k] = fma2(xs, xr[k], ar[k]);
         ai[k] = fma2(xs, xi[k], ai[k]);
       }
-      if (a.eout.kind != 0) sop_pair(a.eout, ar, ai, tile, i, j, act, nact, Ls, Lh);
-      issue_stage<S>(P, g + stride, 1, slot, nb_next[1]);
       ++seq;
     } else {
-      float* tile = reinterpret_cast<float*>(sm + last_slot * a.ctx.slot_bytes);
-      if (a.eout.kind != 0) sop_pair(a.eout, ar, ai, tile, i, j, act, nact, Ls, Lh);
-      issue_stage<S>(P, g + stride, 1, last_slot, nb_next[1]);
+      tslot = (seq - 1) % kSlots;
     }
+    if (a.eout[0].kind != 0)
+      sop_pair<NRC>(a.eout, ar, ai, reinterpret_cast<float*>(sm + tslot * a.ctx.slot_bytes), bi, r, j, act, G, nact, nr,
+               Ls, Lh);
+    // the delayed refill of the tile's slot: the next group's stage kSlots - 1
+    issue_stage<S>(P, g + stride, kSlots - 1, tslot, nb_next[kSlots - 1]);
     if (j + Lh >= Ls) {  // odd Ls: the padding slot stays zero
 #pragma unroll
       for (int k = 0; k < 12; ++k) {
@@ -495,84 +506,120 @@ __global__ void __launch_bounds__(32, 11) hop3_kernel(const Hop3Args<S> a) {
       }
     }
     if (act && !bad) {
-      const long h = h0 + i;
-      store_pair(a.out, h, j, Lh, ar, ai);
-      if (a.partials) {
-        float ps = 0.f;
+      store_pair(pick(a.out, NRC == 1 ? 0 : r), h0 + i, j, Lh, ar, ai);
+      float ps = 0.f;
 #pragma unroll
-        for (int k = 0; k < 12; ++k) {
-          ps = fmaf(ar[k].x, ar[k].x, fmaf(ar[k].y, ar[k].y, ps));
-          ps = fmaf(ai[k].x, ai[k].x, fmaf(ai[k].y, ai[k].y, ps));
-        }
-        part += (double)ps;
+      for (int k = 0; k < 12; ++k) {
+        ps = fmaf(ar[k].x, ar[k].x, fmaf(ar[k].y, ar[k].y, ps));
+        ps = fmaf(ai[k].x, ai[k].x, fmaf(ai[k].y, ai[k].y, ps));
       }
+      part += (double)ps;
     }
 #pragma unroll
     for (int d = 0; d < 8; ++d) nb_cur[d] = nb_next[d];
   }
   if (bad) {
     if (lane == 0) atomicExch(a.err, 1);
-    mbar_wait(P.bar0, (seq >> 1) & 1);  // once more, bounded, for copies still in flight
-    mbar_wait(P.bar0 + 8, (seq >> 1) & 1);
+    for (int s = 0; s < kSlots; ++s) mbar_wait(P.bar0 + 8u * s, ((seq + s) / kSlots) & 1);  // bounded
   }
-  if (a.partials) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-    if (lane == 0) a.partials[blockIdx.x] = part;
+  if (a.partials[0]) {
+    // per right-hand side: sum the lanes (i, r, j) over i and j in a fixed order
+    red[lane] = part;
+    __syncwarp();
+    if (lane < nr) {
+      double t = 0.0;
+      for (int ii = 0; ii < G; ++ii)
+        for (int jj = 0; jj < Lh; ++jj) t += red[ii * NJ + lane * Lh + jj];
+      pick(a.partials, NRC == 1 ? 0 : lane)[blockIdx.x] = t;
+    }
   }
 }
 
 }  // namespace
 
-// Sites per group for the pipelined kernel, or 0 if the shape needs the per-slice kernel.
-int hop2_sites(int Ls, int prec) {
+// Sites per group for the pipelined kernel over nr right-hand sides, or 0 if
+// the shape needs the per-slice kernel.
+int hop2_sites(int Ls, int prec, int nr) {
   const int Lh = (Ls + 1) / 2;
   if (prec != DWF_F32 && prec != DWF_F16) return 0;
-  if (Lh > 32) return 0;
+  if (nr < 1 || nr > kMaxBatch || nr * Lh > 32) return 0;
   if (prec == DWF_F16 && (Lh % 2)) return 0;  // FP16 scale blocks must be multiples of 16 bytes
-  return 32 / Lh;
+  return 32 / (nr * Lh);
+}
+
+// Resident CTAs per SM for a kernel and dynamic smem size (cached).
+static int resident_per_sm(const void* kern, size_t smem, int* per_sm, int* sms_out) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, size_t>, std::pair<int, int>> cache;
+  std::lock_guard<std::mutex> lk(mu);
+  const auto key = std::make_pair(kern, smem);
+  auto it = cache.find(key);
+  if (it != cache.end()) {
+    *per_sm = it->second.first;
+    *sms_out = it->second.second;
+    return 0;
+  }
+  int dev = 0, sms = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 32, smem) != cudaSuccess || per < 1)
+    return 1;
+  cache[key] = std::make_pair(per, sms);
+  *per_sm = per;
+  *sms_out = sms;
+  return 0;
 }
 
 template <class S>
-static dwf_status hop3_t(dwf_lattice* L, const HopCall& c, const SOpK<float>& ex, const SOpK<float>& eout, int G) {
-  Hop3Args<S> a;
-  a.in = CFieldRef<S>{reinterpret_cast<const S*>(c.in.v), c.in.norm};
-  a.out = FieldRef<S>{reinterpret_cast<S*>(c.out.v), c.out.norm};
-  a.x = c.has_x ? CFieldRef<S>{reinterpret_cast<const S*>(c.x.v), c.x.norm} : CFieldRef<S>{nullptr, nullptr};
-  a.links = reinterpret_cast<const S*>(L->links[c.in.prec][c.out_parity]);
+static dwf_status hop3_t(dwf_lattice* L, const HopCall& c, const HopBatch& b, const SOpK<float>* ex,
+                         const SOpK<float>* eout, int G, int ctas_per_sm) {
+  Hop3Args<S> a{};
+  for (int r = 0; r < b.nrhs; ++r) {
+    a.in[r] = CFieldRef<S>{reinterpret_cast<const S*>(b.in[r].v), b.in[r].norm};
+    a.out[r] = FieldRef<S>{reinterpret_cast<S*>(b.out[r].v), b.out[r].norm};
+    a.x[r] = c.has_x ? CFieldRef<S>{reinterpret_cast<const S*>(b.x[r].v), b.x[r].norm} : CFieldRef<S>{nullptr, nullptr};
+    a.ex[r] = ex[r];
+    a.eout[r] = eout[r];
+    a.partials[r] = b.partials[r];
+  }
+  a.links = reinterpret_cast<const S*>(L->links[b.in[0].prec][c.out_parity]);
   a.nbr = L->nbr[c.out_parity];
   a.Vh = L->Vh;
   a.G = G;
+  a.nr = b.nrhs;
   a.ngroups = (L->Vh + G - 1) / G;
   a.Ls = L->Ls;
   a.Lh = L->Lh;
-  a.ctx = make_ctx(L->Ls, c.in.prec, G);
-  a.ex = ex;
-  a.eout = eout;
+  a.ctx = make_ctx(L->Ls, b.in[0].prec, G, b.nrhs);
   a.scale = (float)c.scale;
   a.xscale = (float)c.xscale;
-  a.partials = c.partials;
   a.err = L->dev_err;
-  // persistent grid: enough warps to keep every SM's copy engine and issue slots busy
-  const long want = 152L * 12;
-  const long grid = a.ngroups < want ? a.ngroups : want;
   const size_t smem = (size_t)a.ctx.total;
   auto run = [&](auto kern) -> dwf_status {
     DWF_CUDA(L, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per = 0, sms = 0;
+    if (resident_per_sm(reinterpret_cast<const void*>(kern), smem, &per, &sms))
+      return fail(L, DWF_ERR_CUDA, "hop: occupancy query failed");
+    if (ctas_per_sm > 0 && ctas_per_sm < per) per = ctas_per_sm;
+    const long resident = (long)per * sms;
+    const long grid = a.ngroups < resident ? a.ngroups : resident;  // persistent: one wave
+    if (b.partials[0] && grid > kPartials) return fail(L, DWF_ERR_INVALID_ARG, "partial-sum buffer too small");
     kern<<<(unsigned)grid, 32, smem, L->stream>>>(a);
+    if (c.nblocks) *c.nblocks = (int)grid;
     return DWF_OK;
   };
-  if (c.dag)
-    DWF_TRY(c.has_x ? run(hop3_kernel<S, 1, 1>) : run(hop3_kernel<S, 1, 0>));
-  else
-    DWF_TRY(c.has_x ? run(hop3_kernel<S, 0, 1>) : run(hop3_kernel<S, 0, 0>));
-  if (c.nblocks) *c.nblocks = (int)grid;
-  return DWF_OK;
+  if (b.nrhs == 1) {
+    if (c.dag) return c.has_x ? run(hop3_kernel<S, 1, 1, 1>) : run(hop3_kernel<S, 1, 0, 1>);
+    return c.has_x ? run(hop3_kernel<S, 0, 1, 1>) : run(hop3_kernel<S, 0, 0, 1>);
+  }
+  if (c.dag) return c.has_x ? run(hop3_kernel<S, 1, 1, 0>) : run(hop3_kernel<S, 1, 0, 0>);
+  return c.has_x ? run(hop3_kernel<S, 0, 1, 0>) : run(hop3_kernel<S, 0, 0, 0>);
 }
 
-dwf_status launch_hop2(dwf_lattice* L, const HopCall& c, const SOpK<float>& ex, const SOpK<float>& eout, int G) {
-  if (c.in.prec == DWF_F32) return hop3_t<float>(L, c, ex, eout, G);
-  return hop3_t<__half>(L, c, ex, eout, G);
+dwf_status launch_hop2(dwf_lattice* L, const HopCall& c, const HopBatch& b, const SOpK<float>* ex,
+                       const SOpK<float>* eout, int G, int ctas_per_sm) {
+  if (b.in[0].prec == DWF_F32) return hop3_t<float>(L, c, b, ex, eout, G, ctas_per_sm);
+  return hop3_t<__half>(L, c, b, ex, eout, G, ctas_per_sm);
 }
 
 }  // namespace dwf

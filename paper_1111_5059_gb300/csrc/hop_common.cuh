@@ -138,54 +138,57 @@ __device__ __forceinline__ void tile_get(const C* tile, int R, int i, int s, C* 
   }
 }
 
+// In-place structured operator on one tile row (complex component k of a
+// site, all Ls slices).
+template <class C>
+__device__ __forceinline__ void sop_row(const SOpK<C>& op, C* row, int k, int Ls) {
+  const int up = ((k >= 6) ? 1 : 0) ^ op.trans;  // P+ (k < 6) walks down in s unless transposed
+  const int s0 = up ? Ls - 1 : 0;
+  const int ds = up ? -1 : 1;
+  if (op.has_inv) {
+    C wr = 0, wi = 0;
+    for (int j = 1; j < Ls; ++j) {
+      const C* p = row + 2 * (s0 + ds * j);
+      wr = fma(wr, op.rho, p[0]);
+      wi = fma(wi, op.rho, p[1]);
+    }
+    const C mr = op.m * op.rho;
+    const C z0r = fma(-mr, wr, row[2 * s0]) * op.c0;
+    const C z0i = fma(-mr, wi, row[2 * s0 + 1]) * op.c0;
+    C pr = z0r, pi = z0i;
+    for (int j = 1; j < Ls; ++j) {
+      C* p = row + 2 * (s0 + ds * j);
+      const C zr = fma(op.rho, pr, p[0] * op.ginv);
+      const C zi = fma(op.rho, pi, p[1] * op.ginv);
+      p[0] = fma(op.d1, pr, op.g1 * zr);
+      p[1] = fma(op.d1, pi, op.g1 * zi);
+      pr = zr;
+      pi = zi;
+    }
+    const C dm = op.d1 * op.m;
+    row[2 * s0] = fma(-dm, pr, op.g1 * z0r);
+    row[2 * s0 + 1] = fma(-dm, pi, op.g1 * z0i);
+  } else {
+    // y_j = (g1 x_j + d1 x_{j-1}) / g2 for j >= 1, y_0 = (g1 x_0 - d1 m x_{Ls-1}) / g2
+    C* pl = row + 2 * (s0 + ds * (Ls - 1));
+    const C lr = pl[0], li = pl[1];
+    const C g1 = op.g1 * op.ginv, d1 = op.d1 * op.ginv;
+    for (int j = Ls - 1; j >= 1; --j) {
+      C* p = row + 2 * (s0 + ds * j);
+      const C* q = row + 2 * (s0 + ds * (j - 1));
+      p[0] = fma(d1, q[0], g1 * p[0]);
+      p[1] = fma(d1, q[1], g1 * p[1]);
+    }
+    const C dm = d1 * op.m;
+    row[2 * s0] = fma(-dm, lr, g1 * row[2 * s0]);
+    row[2 * s0 + 1] = fma(-dm, li, g1 * row[2 * s0 + 1]);
+  }
+}
+
 // In-place structured operator on the rows of the first `nsites` sites.
 template <class C>
 __device__ void sop_rows(const SOpK<C>& op, C* tile, int nsites, int Ls, int R) {
-  for (int w = threadIdx.x; w < nsites * 12; w += blockDim.x) {
-    const int k = w % 12;
-    const int up = ((k >= 6) ? 1 : 0) ^ op.trans;  // P+ (k < 6) walks down in s unless transposed
-    C* row = tile + w * R;
-    const int s0 = up ? Ls - 1 : 0;
-    const int ds = up ? -1 : 1;
-    if (op.has_inv) {
-      C wr = 0, wi = 0;
-      for (int j = 1; j < Ls; ++j) {
-        const C* p = row + 2 * (s0 + ds * j);
-        wr = fma(wr, op.rho, p[0]);
-        wi = fma(wi, op.rho, p[1]);
-      }
-      const C mr = op.m * op.rho;
-      const C z0r = fma(-mr, wr, row[2 * s0]) * op.c0;
-      const C z0i = fma(-mr, wi, row[2 * s0 + 1]) * op.c0;
-      C pr = z0r, pi = z0i;
-      for (int j = 1; j < Ls; ++j) {
-        C* p = row + 2 * (s0 + ds * j);
-        const C zr = fma(op.rho, pr, p[0] * op.ginv);
-        const C zi = fma(op.rho, pi, p[1] * op.ginv);
-        p[0] = fma(op.d1, pr, op.g1 * zr);
-        p[1] = fma(op.d1, pi, op.g1 * zi);
-        pr = zr;
-        pi = zi;
-      }
-      const C dm = op.d1 * op.m;
-      row[2 * s0] = fma(-dm, pr, op.g1 * z0r);
-      row[2 * s0 + 1] = fma(-dm, pi, op.g1 * z0i);
-    } else {
-      // y_j = (g1 x_j + d1 x_{j-1}) / g2 for j >= 1, y_0 = (g1 x_0 - d1 m x_{Ls-1}) / g2
-      C* pl = row + 2 * (s0 + ds * (Ls - 1));
-      const C lr = pl[0], li = pl[1];
-      const C g1 = op.g1 * op.ginv, d1 = op.d1 * op.ginv;
-      for (int j = Ls - 1; j >= 1; --j) {
-        C* p = row + 2 * (s0 + ds * j);
-        const C* q = row + 2 * (s0 + ds * (j - 1));
-        p[0] = fma(d1, q[0], g1 * p[0]);
-        p[1] = fma(d1, q[1], g1 * p[1]);
-      }
-      const C dm = d1 * op.m;
-      row[2 * s0] = fma(-dm, lr, g1 * row[2 * s0]);
-      row[2 * s0 + 1] = fma(-dm, li, g1 * row[2 * s0 + 1]);
-    }
-  }
+  for (int w = threadIdx.x; w < nsites * 12; w += blockDim.x) sop_row(op, tile + w * R, w % 12, Ls);
 }
 
 // v (the 24 reals of thread (i, s)) <- op v, across the CTA through the tile.

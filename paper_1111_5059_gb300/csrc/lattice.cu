@@ -33,10 +33,14 @@ size_t field_bytes(const dwf_lattice* L, dwf_prec prec) {
 }
 
 dwf_status check_dev_err(dwf_lattice* L) {
-  int h = 0;
-  DWF_CUDA(L, cudaMemcpy(&h, L->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
-  if (h != 0) {
-    DWF_CUDA(L, cudaMemset(L->dev_err, 0, sizeof(int)));
+  // the last pinned scalar slot receives the flag
+  int* h = reinterpret_cast<int*>(L->hscal + kScalars - 1);
+  *h = 0;
+  DWF_CUDA(L, cudaMemcpyAsync(h, L->dev_err, sizeof(int), cudaMemcpyDeviceToHost, L->stream));
+  DWF_CUDA(L, cudaStreamSynchronize(L->stream));
+  if (*h != 0) {
+    DWF_CUDA(L, cudaMemsetAsync(L->dev_err, 0, sizeof(int), L->stream));
+    DWF_CUDA(L, cudaStreamSynchronize(L->stream));
     return fail(L, DWF_ERR_TIMEOUT, "a bounded device wait gave up (asynchronous copy did not complete)");
   }
   return DWF_OK;

@@ -67,6 +67,22 @@ class MadwfStats(ctypes.Structure):
                 "pass_resid": [self.pass_resid[i] for i in range(self.passes)]}
 
 
+DWF_MAX_RHS = 16
+
+
+class MultiOptions(ctypes.Structure):
+    _fields_ = [("use_graph", ctypes.c_int), ("autotune", ctypes.c_int)]
+
+
+class MultiInfo(ctypes.Structure):
+    _fields_ = [("batch", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("tune_seconds", ctypes.c_double),
+                ("graphs", ctypes.c_int), ("replays", ctypes.c_longlong), ("iterations", ctypes.c_int),
+                ("seconds", ctypes.c_double), ("launches", ctypes.c_longlong)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class Quotient(ctypes.Structure):
     _fields_ = [("m1", ctypes.c_double), ("m2", ctypes.c_double)]
 
@@ -86,6 +102,9 @@ def _declare(lib):
         "dwf_apply_MdagM": [H, ctypes.c_double, _VP, _VP],
         "dwf_apply_Mpc": [H, ctypes.c_double, ctypes.c_int, _VP, _VP],
         "dwf_cg": [H, ctypes.c_double, _VP, _VP, ctypes.POINTER(CGParams), ctypes.POINTER(Stats)],
+        "dwf_cg_multi": [H, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_VP), ctypes.POINTER(_VP),
+                         ctypes.POINTER(CGParams), ctypes.POINTER(MultiOptions), ctypes.POINTER(Stats),
+                         ctypes.POINTER(MultiInfo)],
         "madwf_solve": [H, H, ctypes.c_double, _VP, _VP, ctypes.POINTER(MadwfParams), ctypes.POINTER(MadwfStats)],
         "dwf_apply_Mpc_noalloc": [H, ctypes.c_double, ctypes.c_int, _VP, _VP],
         "dwf_force": [H, ctypes.c_int, ctypes.POINTER(Quotient), ctypes.POINTER(_VP), ctypes.POINTER(_VP), _VP, _VP,
@@ -240,6 +259,27 @@ class Lattice:
         if status != 0 and raise_on_fail:
             _check(status, self._h)
         return SolveResult(x, st.as_dict(), status)
+
+    def cg_multi(self, masses, bs, x0s=None, tol=1e-10, max_iter=100000, inner="f32", delta=0.1, check_every=10,
+                 use_graph=True, autotune=True, raise_on_fail=True):
+        """Solve D(m_r) x_r = b_r for a ladder of masses together (see
+        include/dwf.h, dwf_cg_multi).  Returns (xs, per-RHS stats, info, status)."""
+        n = len(masses)
+        if len(bs) != n or (x0s is not None and len(x0s) != n):
+            raise ValueError("masses, sources and guesses must have the same length")
+        xs = [torch.zeros_like(b) if x0s is None else x0s[i].clone() for i, b in enumerate(bs)]
+        prm = CGParams(float(tol), int(max_iter), _PREC[inner], float(delta), int(check_every))
+        opt = MultiOptions(int(bool(use_graph)), int(bool(autotune)))
+        st = (Stats * n)()
+        info = MultiInfo()
+        ms = (ctypes.c_double * n)(*[float(m) for m in masses])
+        with torch.cuda.device(self.device):
+            status = lib().dwf_cg_multi(self._h, n, ms, _ptr_array(bs, self.spinor_shape),
+                                        _ptr_array(xs, self.spinor_shape), ctypes.byref(prm), ctypes.byref(opt),
+                                        st, ctypes.byref(info))
+        if status != 0 and raise_on_fail:
+            _check(status, self._h)
+        return xs, [st[i].as_dict() for i in range(n)], info.as_dict(), status
 
 
 def madwf_solve(outer: Lattice, inner: Lattice, m: float, b: torch.Tensor, n_dc=3, tol_pv=1e-8, tol_mob=1e-5,

@@ -8,19 +8,28 @@
 // with the fifth-dimension operators of the even-odd Schur form fused).
 //
 // GB300 design:
-//  * Thread (i, j) owns the slice pair (j, j + Lh) of 4D site i, so both
-//    lanes of every packed FP32x2 FMA (__ffma2_rn) use the same link element.
-//  * A CTA is one warp that walks a stream of site groups (G = 32 / Lh sites
-//    per group).  A group is a sequence of stages: the 8 directions (the G
-//    neighbour blocks of that direction -- a neighbour's 5D spinor block is
-//    contiguous in the pair layout; stage 0 also brings the group's links)
-//    and, if the hop has a site term, the group's own block.  Stages are
-//    fetched by the bulk copy engine (cp.async.bulk, completion counted on an
-//    mbarrier per slot) into a ring of kSlots shared-memory slots in issue
-//    order, so kSlots - 1 stages are in flight while one is computed, across
-//    group boundaries, independently of occupancy; no block barrier exists.
+//  * Thread (i, r, j) owns the slice pair (j, j + Lh) of 4D site i of
+//    right-hand side r, so both lanes of every packed FP32x2 FMA
+//    (__ffma2_rn) use the same link element.  One launch may cover up to
+//    kMaxBatch right-hand sides (a mass ladder) that share the links.
+//  * A CTA is one warp that walks a stream of site groups (G sites of every
+//    right-hand side per group, G * nr * Lh <= 32).  A group is a sequence
+//    of stages: the 8 directions (the neighbour blocks of that direction --
+//    a neighbour's 5D spinor block is contiguous in the pair layout, and the
+//    neighbours of consecutive sites are usually consecutive, so a stage is
+//    one bulk copy per right-hand side; stage 0 also brings the group's
+//    links) and, if the hop has a site term, the group's own blocks.  Stages
+//    are fetched by the bulk copy engine (cp.async.bulk, completion counted
+//    on an mbarrier per slot) into a ring of kSlots shared-memory slots in
+//    issue order, across group boundaries; no block barrier exists.  Two
+//    slots (one stage in flight per warp) leave room for more resident warps,
+//    which measured faster than deeper rings.
 //  * Links are read once per group from shared memory and reused over all Ls
-//    slices; the s-op tile of the epilogue reuses the slot just consumed.
+//    slices (and right-hand sides).
+//  * The fifth-dimension epilogue stays in registers for even Ls: the s
+//    recurrence of an inverse is a log-depth scan across the site's lanes by
+//    warp shuffles; odd Ls and dense fallbacks go through a shared-memory
+//    tile in the slot just consumed.
 //  * Waits on the mbarriers are bounded: a wait that gives up sets the
 //    handle's device error flag (reported as DWF_ERR_TIMEOUT), waits once more
 //    for the warp's own copies and skips the store.
@@ -36,7 +45,7 @@ namespace dwf {
 namespace {
 
 constexpr long kWaitLimit = 1L << 22;
-constexpr int kSlots = 3;
+constexpr int kSlots = 2;
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) {
   return static_cast<unsigned>(__cvta_generic_to_shared(p));
@@ -183,12 +192,116 @@ template <class T> __device__ __forceinline__ T pick(const T* arr, int r) {
   return v;
 }
 
+// y <- op y on the slice pairs a lane holds, for a structured operator and
+// even Ls >= 2, without shared memory: the Ls slices of a site live in its Lh
+// lanes base .. base + Lh - 1 (slice j in .x, slice j + Lh in .y of lane
+// base + j).  With u = x / g2, the inverse (g2 + d2 Q)^-1 is the first-order
+// recurrence z_s = rho z_{s-1} + u_s closed by the wall term -m: a log-depth
+// scan across the lanes gives the open prefix P_s, the two halves are joined
+// by P_{Lh-1}, and the wall adds rho^s w with w = -rho m P_{Ls-1} / (1 + m rho^Ls).
+// Rows that walk down in s (P- rows, or P+ rows of a transposed operator) use
+// the mirrored suffix form.  y = g1 z + d1 Q z then needs one neighbouring
+// slice, one shuffle away.
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+
+__device__ __forceinline__ void sop_shfl(const SOpK<float>& op, float2* re, float2* im, int j, int Lh) {
+  constexpr unsigned F = 0xffffffffu;
+  const int lane = threadIdx.x, base = lane - j;
+  const float rho = op.rho, m = op.m;
+  // lane powers of rho: rho^j, rho^Lh, rho^(Lh-j), rho^(Lh-1-j)
+  float pj = 1.f, pL = 1.f, pLj = 1.f, pLj1 = 1.f;
+  if (op.has_inv)
+    for (int q = 0; q < Lh; ++q) {
+      pL *= rho;
+      if (q < j) pj *= rho;
+      if (q >= j) pLj *= rho;
+      if (q > j) pLj1 *= rho;
+    }
+  const float wk = op.has_inv ? -rho * m * (op.c0 / op.ginv) : 0.f;  // -rho m / (1 + m rho^Ls)
+#pragma unroll
+  for (int half = 0; half < 2; ++half) {
+    const int up = half ^ op.trans;  // 0: z_s from z_{s-1} (prefix); 1: from z_{s+1} (suffix)
+    float2* R = re + 6 * half;
+    float2* I = im + 6 * half;
+    const float2 gi = f2(op.ginv);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      R[k] = mul2(gi, R[k]);
+      I[k] = mul2(gi, I[k]);
+    }
+    if (op.has_inv) {
+      float rd = rho;
+      for (int d = 1; d < Lh; d <<= 1) {
+        const bool ok = up ? (j + d < Lh) : (j >= d);
+        const int src = ok ? (up ? lane + d : lane - d) : lane;
+        const float2 f = f2(ok ? rd : 0.f);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+          const float2 tr = make_float2(__shfl_sync(F, R[k].x, src), __shfl_sync(F, R[k].y, src));
+          const float2 ti = make_float2(__shfl_sync(F, I[k].x, src), __shfl_sync(F, I[k].y, src));
+          R[k] = fma2(f, tr, R[k]);
+          I[k] = fma2(f, ti, I[k]);
+        }
+        rd *= rd;
+      }
+      if (!up) {
+        // second half += rho^(j+1) P_{Lh-1}; then the wall, P_{Ls-1} in .y of the last lane
+        const float cf = pj * rho;
+        const float2 ps = make_float2(pj, pj * pL);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+          R[k].y = fmaf(cf, __shfl_sync(F, R[k].x, base + Lh - 1), R[k].y);
+          I[k].y = fmaf(cf, __shfl_sync(F, I[k].x, base + Lh - 1), I[k].y);
+        }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+          R[k] = fma2(ps, f2(wk * __shfl_sync(F, R[k].y, base + Lh - 1)), R[k]);
+          I[k] = fma2(ps, f2(wk * __shfl_sync(F, I[k].y, base + Lh - 1)), I[k]);
+        }
+      } else {
+        // first half += rho^(Lh-j) S_{Lh}; then the wall, S_0 in .x of the first lane
+        const float2 ps = make_float2(pLj1 * pL, pLj1);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+          R[k].x = fmaf(pLj, __shfl_sync(F, R[k].y, base), R[k].x);
+          I[k].x = fmaf(pLj, __shfl_sync(F, I[k].y, base), I[k].x);
+        }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+          R[k] = fma2(ps, f2(wk * __shfl_sync(F, R[k].x, base)), R[k]);
+          I[k] = fma2(ps, f2(wk * __shfl_sync(F, I[k].x, base)), I[k]);
+        }
+      }
+    }
+    // y = g1 z + d1 Q z: the neighbouring slice, or -m times the other wall
+    const bool edge = up ? (j == Lh - 1) : (j == 0);
+    const int src = up ? (edge ? base : lane + 1) : (edge ? base + Lh - 1 : lane - 1);
+    const float2 g1 = f2(op.g1), d1 = f2(op.d1);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const float ar = __shfl_sync(F, R[k].x, src), br = __shfl_sync(F, R[k].y, src);
+      const float ai = __shfl_sync(F, I[k].x, src), bi = __shfl_sync(F, I[k].y, src);
+      float2 qr = make_float2(ar, br), qi = make_float2(ai, bi);
+      if (edge) {
+        qr = up ? make_float2(br, -m * ar) : make_float2(-m * br, ar);
+        qi = up ? make_float2(bi, -m * ai) : make_float2(-m * bi, ai);
+      }
+      R[k] = fma2(d1, qr, mul2(g1, R[k]));
+      I[k] = fma2(d1, qi, mul2(g1, I[k]));
+    }
+  }
+}
+
 // (re, im) <- ops[r] (re, im) across the warp, through the tile (all lanes
 // call).  Tile block bi = r * G + i holds site i of right-hand side r; all
 // right-hand sides of a launch share the operator kind.
 template <int NRC>
 __device__ __forceinline__ void sop_pair(const SOpK<float>* ops, float2* re, float2* im, float* tile, int bi, int r,
                                          int j, bool act, int G, int nact, int nr, int Ls, int Lh) {
+  if (ops[0].kind == 1 && !(Ls & 1)) {  // registers and shuffles only (every lane calls)
+    sop_shfl(pick(ops, NRC == 1 ? 0 : r), re, im, j, Lh);
+    return;
+  }
   const int R = tile_row(Ls);
   if (act) tile_put_pair(tile, R, bi, j, Lh, Ls, re, im);
   __syncwarp();
@@ -239,12 +352,13 @@ struct Ctx {        // per-CTA shared-memory layout (byte offsets)
   int total;
 };
 
-__host__ __device__ inline Ctx make_ctx(int Ls, int prec, int G, int nr) {
+// need_tile: an epilogue runs through shared memory (odd Ls or a dense operator)
+__host__ __device__ inline Ctx make_ctx(int Ls, int prec, int G, int nr, bool need_tile) {
   const int Lh = (Ls + 1) / 2;
   const int cb = prec == DWF_F32 ? 16 : 8;
   const int nb = G * nr;
   const int blocks = nb * 12 * Lh * cb + (prec == DWF_F16 ? nb * Lh * 8 : 0);
-  const int tile = nb * 12 * tile_row(Ls) * 4;
+  const int tile = need_tile ? nb * 12 * tile_row(Ls) * 4 : 0;
   int slot = blocks > tile ? blocks : tile;
   slot = (slot + 127) / 128 * 128;
   Ctx c;
@@ -283,6 +397,8 @@ template <class S> struct Pipe {
   const unsigned char* src_in_n;  // its FP16 scales
   const unsigned char* src_x;     // x[lane] (lane < nr)
   const unsigned char* src_x_n;
+  const unsigned char* src_run;   // in[lane] (lane < nr): whole-group copies
+  const unsigned char* src_run_n;
 };
 
 // Issue stage k of group g into ring slot `slot` (all lanes call).  Slot
@@ -307,7 +423,19 @@ __device__ __forceinline__ void issue_stage(const Pipe<S>& P, long g, int k, int
   if (lane == 0) mbar_expect_tx(bar, bytes);
   __syncwarp();
   if (k < 8) {
-    if (lane < nb && lane % a.G < nact) {
+    // When the group's neighbours in this direction are consecutive sites (a
+    // group inside one x-row, whose y/z/t neighbours shift as a block), one
+    // copy per right-hand side moves them all; otherwise one copy per site.
+    const int nb0 = __shfl_sync(0xffffffffu, nb_k, 0);
+    const unsigned run = __ballot_sync(0xffffffffu, lane >= nact || nb_k == nb0 + lane);
+    if (run == 0xffffffffu) {
+      if (lane < P.nr) {
+        bulk_g2s(smem_addr(dst + lane * a.G * P.blk), P.src_run + (long)nb0 * P.blk, nact * P.blk, bar);
+        if (fp16)
+          bulk_g2s(smem_addr(dst + nb * P.blk + lane * a.G * P.sblk), P.src_run_n + (long)nb0 * P.sblk,
+                   nact * P.sblk, bar);
+      }
+    } else if (lane < nb && lane % a.G < nact) {
       bulk_g2s(smem_addr(dst + lane * P.blk), P.src_in + (long)nb_k * P.blk, P.blk, bar);
       if (fp16) bulk_g2s(smem_addr(dst + nb * P.blk + lane * P.sblk), P.src_in_n + (long)nb_k * P.sblk, P.sblk, bar);
     }
@@ -370,7 +498,7 @@ __device__ __forceinline__ void site_links(const Pipe<S>& P, int lb, int i, int 
 // Lane (i, r, j) = lane / (nr Lh), ... owns slice pair j of site i of
 // right-hand side r; a group is G consecutive sites of all nr right-hand sides.
 template <class S, int DAG, int HX, int NRC>
-__global__ void __launch_bounds__(32, 8) hop3_kernel(const Hop3Args<S> a) {
+__global__ void __launch_bounds__(32, 10) hop3_kernel(const Hop3Args<S> a) {
   extern __shared__ __align__(128) unsigned char sm[];
   __shared__ __align__(8) unsigned long long bars[kSlots];
   __shared__ double red[32];
@@ -397,6 +525,9 @@ __global__ void __launch_bounds__(32, 8) hop3_kernel(const Hop3Args<S> a) {
     const CFieldRef<S> fx = pick(a.x, (NRC == 1 || lane >= nr) ? 0 : lane);
     P.src_x = reinterpret_cast<const unsigned char*>(fx.v);
     P.src_x_n = reinterpret_cast<const unsigned char*>(fx.norm);
+    const CFieldRef<S> fr = pick(a.in, (NRC == 1 || lane >= nr) ? 0 : lane);
+    P.src_run = reinterpret_cast<const unsigned char*>(fr.v);
+    P.src_run_n = reinterpret_cast<const unsigned char*>(fr.norm);
   }
   if (lane == 0) {
     for (int s = 0; s < kSlots; ++s) mbar_init(P.bar0 + 8u * s, 1);
@@ -590,7 +721,9 @@ static dwf_status hop3_t(dwf_lattice* L, const HopCall& c, const HopBatch& b, co
   a.ngroups = (L->Vh + G - 1) / G;
   a.Ls = L->Ls;
   a.Lh = L->Lh;
-  a.ctx = make_ctx(L->Ls, b.in[0].prec, G, b.nrhs);
+  const bool dense = (c.has_x && ex[0].kind == 2) || eout[0].kind == 2;
+  const bool any = (c.has_x && ex[0].kind != 0) || eout[0].kind != 0;
+  a.ctx = make_ctx(L->Ls, b.in[0].prec, G, b.nrhs, any && ((L->Ls & 1) || dense));
   a.scale = (float)c.scale;
   a.xscale = (float)c.xscale;
   a.err = L->dev_err;

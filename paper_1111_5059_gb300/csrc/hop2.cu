@@ -79,54 +79,39 @@ __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.a
 
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
-// z = a + c*b for c in {+1, -1, +i, -i} on complex pairs (re, im as float2 over slices)
+// z = a + c b on complex pairs, c = sg * (CR + i CI) with the unit (CR, CI)
+// fixed at compile time and the sign sg = +-1 at run time (sgp = (sg, sg)).
 template <int CR, int CI>
-__device__ __forceinline__ void cpair(float2 ar, float2 ai, float2 br, float2 bi, float2& zr, float2& zi) {
-  if constexpr (CR == 1) {
-    zr = add2(ar, br);
-    zi = add2(ai, bi);
-  } else if constexpr (CR == -1) {
-    zr = sub2(ar, br);
-    zi = sub2(ai, bi);
-  } else if constexpr (CI == 1) {
-    zr = sub2(ar, bi);
-    zi = add2(ai, br);
+__device__ __forceinline__ void cpair_s(float2 sgp, float2 ar, float2 ai, float2 br, float2 bi, float2& zr,
+                                        float2& zi) {
+  if constexpr (CI == 0) {
+    const float2 c = CR == 1 ? sgp : make_float2(-sgp.x, -sgp.y);
+    zr = fma2(c, br, ar);
+    zi = fma2(c, bi, ai);
   } else {
-    zr = add2(ar, bi);
-    zi = sub2(ai, br);
-  }
-}
-// acc += c * g
-template <int CR, int CI>
-__device__ __forceinline__ void cacc(float2& ar, float2& ai, float2 gr, float2 gi) {
-  if constexpr (CR == 1) {
-    ar = add2(ar, gr);
-    ai = add2(ai, gi);
-  } else if constexpr (CR == -1) {
-    ar = sub2(ar, gr);
-    ai = sub2(ai, gi);
-  } else if constexpr (CI == 1) {
-    ar = sub2(ar, gi);
-    ai = add2(ai, gr);
-  } else {
-    ar = add2(ar, gi);
-    ai = sub2(ai, gr);
+    const float2 c = CI == 1 ? sgp : make_float2(-sgp.x, -sgp.y);
+    zr = fma2(make_float2(-c.x, -c.y), bi, ar);
+    zi = fma2(c, br, ai);
   }
 }
 
-// acc += (1 - SG g_MU) U psi on a slice pair; psi given by (pr, pi)[12],
-// link U as 9 complex (ur, ui), broadcast to both lanes.
-template <int MU, int SG>
-__device__ __forceinline__ void hop_dir2(const float2* pr, const float2* pi, const float2* U, float2* ar, float2* ai) {
-  typedef Proj<MU, SG> P;
+// acc += (1 - sg g_MU) U psi on a slice pair; psi given by (pr, pi)[12], link
+// U as 9 complex (ur, ui), broadcast to both lanes.  Every coefficient of the
+// projector is proportional to sg, so one body serves both signs (forward
+// and backward neighbours, and the dagger), which keeps the kernel's code
+// small enough for the instruction cache.
+template <int MU>
+__device__ __forceinline__ void hop_dir2(float sg, const float2* pr, const float2* pi, const float2* U, float2* ar,
+                                         float2* ai) {
+  typedef Proj<MU, 1> P;
+  const float2 sgp = f2(sg);
   float2 hr[6], hi[6];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    cpair<P::C1R, P::C1I>(pr[a], pi[a], pr[P::J1 * 3 + a], pi[P::J1 * 3 + a], hr[a], hi[a]);
-    cpair<P::C2R, P::C2I>(pr[3 + a], pi[3 + a], pr[P::J2 * 3 + a], pi[P::J2 * 3 + a], hr[3 + a], hi[3 + a]);
+    cpair_s<P::C1R, P::C1I>(sgp, pr[a], pi[a], pr[P::J1 * 3 + a], pi[P::J1 * 3 + a], hr[a], hi[a]);
+    cpair_s<P::C2R, P::C2I>(sgp, pr[3 + a], pi[3 + a], pr[P::J2 * 3 + a], pi[P::J2 * 3 + a], hr[3 + a], hi[3 + a]);
   }
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
@@ -138,20 +123,31 @@ __device__ __forceinline__ void hop_dir2(const float2* pr, const float2* pi, con
     }
 #pragma unroll
     for (int hh = 0; hh < 2; ++hh) {
-      // g = sum_b U_ab h_b :  gr = sum ur hr - sum ui hi,  gi = sum ur hi + ui hr
-      float2 A = make_float2(0.f, 0.f), B = A, gi = A;
+      // g = sum_b U_ab h_b :  gr = sum ur hr - sum ui hi,  gi = sum ur hi + sum ui hr
+      float2 A = make_float2(0.f, 0.f), B = A, C = A, D = A;
 #pragma unroll
       for (int b = 0; b < 3; ++b) {
         A = fma2(ur[b], hr[3 * hh + b], A);
         B = fma2(ui[b], hi[3 * hh + b], B);
-        gi = fma2(ur[b], hi[3 * hh + b], gi);
-        gi = fma2(ui[b], hr[3 * hh + b], gi);
+        C = fma2(ur[b], hi[3 * hh + b], C);
+        D = fma2(ui[b], hr[3 * hh + b], D);
       }
-      const float2 gr = sub2(A, B);
+      const float2 gr = fma2(f2(-1.f), B, A), gi = add2(C, D);
       ar[3 * hh + a] = add2(ar[3 * hh + a], gr);  // upper spins 0, 1
       ai[3 * hh + a] = add2(ai[3 * hh + a], gi);
-      if (hh == P::S2) cacc<P::D2R, P::D2I>(ar[6 + a], ai[6 + a], gr, gi);  // lower spins 2, 3
-      if (hh == P::S3) cacc<P::D3R, P::D3I>(ar[9 + a], ai[9 + a], gr, gi);
+      // lower spins 2, 3: += d g with d = sg * (DR + i DI)
+      if (hh == P::S2) {
+        float2 zr, zi;
+        cpair_s<P::D2R, P::D2I>(sgp, ar[6 + a], ai[6 + a], gr, gi, zr, zi);
+        ar[6 + a] = zr;
+        ai[6 + a] = zi;
+      }
+      if (hh == P::S3) {
+        float2 zr, zi;
+        cpair_s<P::D3R, P::D3I>(sgp, ar[9 + a], ai[9 + a], gr, gi, zr, zi);
+        ar[9 + a] = zr;
+        ai[9 + a] = zi;
+      }
     }
   }
 }
@@ -349,6 +345,7 @@ struct Ctx {        // per-CTA shared-memory layout (byte offsets)
   int slot_bytes;   // one ring slot: G x nr site blocks (+ FP16 scales), or the s-op tile
   int raw_off;      // two link buffers (groups alternate), one padded block per site
   int link_stride;  // bytes between two sites' link blocks
+  int nb_off;       // neighbour indices [2 groups][8 directions][G nr copy lanes]
   int total;
 };
 
@@ -366,7 +363,8 @@ __host__ __device__ inline Ctx make_ctx(int Ls, int prec, int G, int nr, bool ne
   c.raw_off = kSlots * slot;
   // 8 links x 18 reals per site, +16 bytes so consecutive sites start in different banks
   c.link_stride = 8 * 18 * (prec == DWF_F32 ? 4 : 2) + 16;
-  c.total = c.raw_off + 2 * G * c.link_stride;
+  c.nb_off = c.raw_off + 2 * G * c.link_stride;
+  c.total = c.nb_off + 2 * 8 * nb * 4;
   return c;
 }
 
@@ -393,6 +391,7 @@ template <class S> struct Pipe {
   unsigned bar0;
   int blk, sblk;
   int nr;                         // right-hand sides of the launch
+  int* nbs;                       // neighbour table in shared memory
   const unsigned char* src_in;    // this lane's copy source: in[lane / G] (lane < G nr)
   const unsigned char* src_in_n;  // its FP16 scales
   const unsigned char* src_x;     // x[lane] (lane < nr)
@@ -403,9 +402,9 @@ template <class S> struct Pipe {
 
 // Issue stage k of group g into ring slot `slot` (all lanes call).  Slot
 // block t = r * G + i holds site i of right-hand side r and is fetched by
-// lane t; nb_k is the neighbour index of that site for direction k (k < 8).
+// lane t; the group's neighbour indices and links sit in buffer lb.
 template <class S>
-__device__ __forceinline__ void issue_stage(const Pipe<S>& P, long g, int k, int slot, int nb_k) {
+__device__ __forceinline__ void issue_stage(const Pipe<S>& P, long g, int k, int slot, int lb) {
   const Hop3Args<S>& a = *P.a;
   if (g >= a.ngroups) return;
   const long h0 = g * a.G;
@@ -423,6 +422,7 @@ __device__ __forceinline__ void issue_stage(const Pipe<S>& P, long g, int k, int
   if (lane == 0) mbar_expect_tx(bar, bytes);
   __syncwarp();
   if (k < 8) {
+    const int nb_k = lane < nb ? P.nbs[(lb * 8 + k) * nb + lane] : 0;
     // When the group's neighbours in this direction are consecutive sites (a
     // group inside one x-row, whose y/z/t neighbours shift as a block), one
     // copy per right-hand side moves them all; otherwise one copy per site.
@@ -442,7 +442,6 @@ __device__ __forceinline__ void issue_stage(const Pipe<S>& P, long g, int k, int
     if (k == 0 && lane < nact) {
       // the links of consecutive groups of this CTA alternate between two
       // buffers: this copy is issued while the previous group still reads its own
-      const int lb = (int)(((g - blockIdx.x) / gridDim.x) & 1);
       bulk_g2s(smem_addr(P.sm + a.ctx.raw_off + (lb * a.G + lane) * a.ctx.link_stride),
                a.links + (h0 + lane) * 8 * 18, lbytes, bar);
     }
@@ -498,7 +497,7 @@ __device__ __forceinline__ void site_links(const Pipe<S>& P, int lb, int i, int 
 // Lane (i, r, j) = lane / (nr Lh), ... owns slice pair j of site i of
 // right-hand side r; a group is G consecutive sites of all nr right-hand sides.
 template <class S, int DAG, int HX, int NRC>
-__global__ void __launch_bounds__(32, 10) hop3_kernel(const Hop3Args<S> a) {
+__global__ void __launch_bounds__(32, 12) hop3_kernel(const Hop3Args<S> a) {
   extern __shared__ __align__(128) unsigned char sm[];
   __shared__ __align__(8) unsigned long long bars[kSlots];
   __shared__ double red[32];
@@ -517,6 +516,7 @@ __global__ void __launch_bounds__(32, 10) hop3_kernel(const Hop3Args<S> a) {
   P.blk = 12 * Lh * chunk_bytes<S>();
   P.sblk = Lh * 8;
   P.nr = nr;
+  P.nbs = reinterpret_cast<int*>(sm + a.ctx.nb_off);
   {
     const int rc = (NRC == 1 || lane >= G * nr) ? 0 : lane / G;
     const CFieldRef<S> fin = pick(a.in, rc);
@@ -535,40 +535,37 @@ __global__ void __launch_bounds__(32, 10) hop3_kernel(const Hop3Args<S> a) {
   }
   __syncwarp();
   const long stride = gridDim.x;
-  // neighbour indices of the current and the next group for this lane's copy site
-  int nb_cur[8], nb_next[8];
-  auto load_nb = [&](long g, int* nb) {
-#pragma unroll
-    for (int d = 0; d < 8; ++d) nb[d] = 0;
-    if (g < a.ngroups && lane < G * nr) {
+  // neighbour indices of a group for this lane's copy site, into buffer lb
+  // (each lane reads back only what it wrote)
+  auto load_nb = [&](long g, int lb) {
+    if (lane < G * nr) {
       const long hh = g * G + lane % G;
-      if (hh < a.Vh) {
+      const bool ok = g < a.ngroups && hh < a.Vh;
 #pragma unroll
-        for (int d = 0; d < 8; ++d) nb[d] = __ldg(a.nbr + (long)d * a.Vh + hh);
-      }
+      for (int d = 0; d < 8; ++d) P.nbs[(lb * 8 + d) * G * nr + lane] = ok ? __ldg(a.nbr + (long)d * a.Vh + hh) : 0;
     }
   };
   long g = blockIdx.x;
-  load_nb(g, nb_cur);
+  load_nb(g, 0);
 #pragma unroll
-  for (int s = 0; s < kSlots; ++s) issue_stage<S>(P, g, s, s, nb_cur[s]);
+  for (int s = 0; s < kSlots; ++s) issue_stage<S>(P, g, s, s, 0);
   unsigned seq = 0;  // global index of the stage being consumed; slot seq % kSlots
   bool bad = false;
   double part = 0.0;
-  for (; g < a.ngroups; g += stride) {
-    load_nb(g + stride, nb_next);
+  int lb = 0;  // this group's link / neighbour buffer; groups of a CTA alternate
+  for (; g < a.ngroups; g += stride, lb ^= 1) {
+    load_nb(g + stride, lb ^ 1);
     const long h0 = g * G;
     const long left = a.Vh - h0;
     const int nact = left < G ? (int)left : G;
     const bool act = i < nact;
-    const int lb = (int)(((g - blockIdx.x) / stride) & 1);
     float2 ar[12], ai[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
       ar[k] = make_float2(0.f, 0.f);
       ai[k] = ar[k];
     }
-#pragma unroll
+#pragma unroll 1
     for (int d = 0; d < 8; ++d) {
       const int slot = seq % kSlots;
       if (!mbar_wait(P.bar0 + 8u * slot, (seq / kSlots) & 1)) bad = true;
@@ -576,15 +573,14 @@ __global__ void __launch_bounds__(32, 10) hop3_kernel(const Hop3Args<S> a) {
         float2 pr[12], pi[12], U[9];
         read_pair<S>(P, sm + slot * a.ctx.slot_bytes, bi, j, pr, pi);
         site_links<S>(P, lb, i, d, U);
-        constexpr int F = DAG ? -1 : 1;
-        if (d == 0) hop_dir2<0, F>(pr, pi, U, ar, ai);
-        if (d == 1) hop_dir2<1, F>(pr, pi, U, ar, ai);
-        if (d == 2) hop_dir2<2, F>(pr, pi, U, ar, ai);
-        if (d == 3) hop_dir2<3, F>(pr, pi, U, ar, ai);
-        if (d == 4) hop_dir2<0, -F>(pr, pi, U, ar, ai);
-        if (d == 5) hop_dir2<1, -F>(pr, pi, U, ar, ai);
-        if (d == 6) hop_dir2<2, -F>(pr, pi, U, ar, ai);
-        if (d == 7) hop_dir2<3, -F>(pr, pi, U, ar, ai);
+        // (1 - sg g_mu): sg = +1 forward / -1 backward, flipped by the dagger
+        const float sg = ((d < 4) != (DAG != 0)) ? 1.f : -1.f;
+        switch (d & 3) {
+          case 0: hop_dir2<0>(sg, pr, pi, U, ar, ai); break;
+          case 1: hop_dir2<1>(sg, pr, pi, U, ar, ai); break;
+          case 2: hop_dir2<2>(sg, pr, pi, U, ar, ai); break;
+          default: hop_dir2<3>(sg, pr, pi, U, ar, ai); break;
+        }
       }
       __syncwarp();
       // refill this slot with the stage kSlots ahead; after the group's last
@@ -592,9 +588,9 @@ __global__ void __launch_bounds__(32, 10) hop3_kernel(const Hop3Args<S> a) {
       if (d != NST - 1) {
         const int k2 = d + kSlots;
         if (k2 < NST)
-          issue_stage<S>(P, g, k2, slot, nb_cur[k2 < 8 ? k2 : 0]);
+          issue_stage<S>(P, g, k2, slot, lb);
         else
-          issue_stage<S>(P, g + stride, k2 - NST, slot, nb_next[k2 - NST < 8 ? k2 - NST : 0]);
+          issue_stage<S>(P, g + stride, k2 - NST, slot, lb ^ 1);
       }
       ++seq;
     }
@@ -628,7 +624,7 @@ __global__ void __launch_bounds__(32, 10) hop3_kernel(const Hop3Args<S> a) {
       sop_pair<NRC>(a.eout, ar, ai, reinterpret_cast<float*>(sm + tslot * a.ctx.slot_bytes), bi, r, j, act, G, nact, nr,
                Ls, Lh);
     // the delayed refill of the tile's slot: the next group's stage kSlots - 1
-    issue_stage<S>(P, g + stride, kSlots - 1, tslot, nb_next[kSlots - 1]);
+    issue_stage<S>(P, g + stride, kSlots - 1, tslot, lb ^ 1);
     if (j + Lh >= Ls) {  // odd Ls: the padding slot stays zero
 #pragma unroll
       for (int k = 0; k < 12; ++k) {
@@ -638,16 +634,14 @@ __global__ void __launch_bounds__(32, 10) hop3_kernel(const Hop3Args<S> a) {
     }
     if (act && !bad) {
       store_pair(pick(a.out, NRC == 1 ? 0 : r), h0 + i, j, Lh, ar, ai);
-      float ps = 0.f;
+      float2 p0 = make_float2(0.f, 0.f), p1 = p0;
 #pragma unroll
       for (int k = 0; k < 12; ++k) {
-        ps = fmaf(ar[k].x, ar[k].x, fmaf(ar[k].y, ar[k].y, ps));
-        ps = fmaf(ai[k].x, ai[k].x, fmaf(ai[k].y, ai[k].y, ps));
+        p0 = fma2(ar[k], ar[k], p0);
+        p1 = fma2(ai[k], ai[k], p1);
       }
-      part += (double)ps;
+      part += (double)((p0.x + p0.y) + (p1.x + p1.y));
     }
-#pragma unroll
-    for (int d = 0; d < 8; ++d) nb_cur[d] = nb_next[d];
   }
   if (bad) {
     if (lane == 0) atomicExch(a.err, 1);

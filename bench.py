@@ -34,6 +34,11 @@ sys.path.insert(0, ROOT)
 
 HBM_FALLBACK_GBS = 6800.0
 
+# DRAM traffic per algorithmic byte of the FP32 hop kernel, from one ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum of two launches on the
+# 24^3x48x16 Ls=16 case); it applies only to the kernel source it was taken on.
+HOP_TRAFFIC = {"source_sha256_prefix": "980679d16f54a3b2", "ratio": 1.086}
+
 WORKLOADS = {
     # MADWF: Shamir 24^3 x 64 x Ls=32, m_f = 0.002, eps = 0.6, through Moebius Ls' = 12 with
     # b - c = 1 and b + c = Ls / Ls' (b = 11/6, c = 5/6); 3 defect-correction passes.
@@ -69,6 +74,21 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tol", type=float, default=1e-10)
     return ap.parse_args()
+
+
+def hop_traffic(bytes_per_launch):
+    """DRAM bytes per launch of the FP32 hop (scaled from the ncu capture), or
+    None if the kernel source differs from the one that was measured."""
+    import hashlib
+
+    try:
+        with open(os.path.join(ROOT, "paper_1111_5059_gb300", "csrc", "hop2.cu"), "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()[:16]
+    except OSError:
+        return None
+    if sha != HOP_TRAFFIC["source_sha256_prefix"]:
+        return None
+    return bytes_per_launch * HOP_TRAFFIC["ratio"]
 
 
 def measured_peak():
@@ -325,7 +345,8 @@ def run_ladder(args, w, inner, world, rank, local, dev, hbm_peak, peak_src):
     st, info = stats[-1], infos[-1]
     achieved = kt["bytes"] / (kt["ms"] / 1e3) / 1e9 if kt["ms"] > 0 else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-            "frac": (achieved / hbm_peak) if achieved else None, "traffic": None,
+            "frac": (achieved / hbm_peak) if achieved else None,
+            "traffic": hop_traffic(kt["bytes"] / max(1, kt["launches"])) if inner == "f32" else None,
             "kernel": f"hop3_kernel<{inner}> batched over right-hand sides (Wilson hop at every s, fused "
                       "fifth-dimension epilogues per mass)",
             "launches": kt["launches"], "avg_launch_us": kt["ms"] / max(1, kt["launches"]) * 1e3,
@@ -471,8 +492,10 @@ def main():
 
     achieved = kt["bytes"] / (kt["ms"] / 1e3) / 1e9 if kt["ms"] > 0 else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-            "frac": (achieved / hbm_peak) if achieved else None, "traffic": None,
-            "kernel": f"hop_kernel<{inner}> (Wilson hop at every s with fused fifth-dimension epilogues)",
+            "frac": (achieved / hbm_peak) if achieved else None,
+            "traffic": hop_traffic(kt["bytes"] / max(1, kt["launches"])) if inner == "f32" else None,
+            "traffic_source": "ncu DRAM read+write per algorithmic byte on 24^3x48x16 Ls=16, scaled to this launch size",
+            "kernel": f"hop3_kernel<{inner}> (Wilson hop at every s with fused fifth-dimension epilogues)",
             "launches": kt["launches"], "avg_launch_us": kt["ms"] / max(1, kt["launches"]) * 1e3,
             "bytes_per_launch": kt["bytes"] / max(1, kt["launches"]),
             "share_of_step": kt["ms"] / max(1e-9, sum(step_ms)),

@@ -118,31 +118,24 @@ __global__ void __launch_bounds__(kBlasThreads) k_axpby_p(double a, CFieldRef<SX
   }
 }
 
-// ---- x += alpha p; r -= alpha q; partial |r|^2   (x may be stored at a higher precision)
-template <class S, class SX>
-__global__ void __launch_bounds__(kBlasThreads) k_cg_xr_c(const double* alpha, CFieldRef<S> p, CFieldRef<S> q,
-                                                         FieldRef<SX> x, FieldRef<S> r, long nq, int Lh,
-                                                         double* partials) {
+// ---- r -= alpha q; partial |r|^2   (the CG residual update; x moves with p below)
+template <class S>
+__global__ void __launch_bounds__(kBlasThreads) k_cg_r_c(const double* alpha, CFieldRef<S> q, FieldRef<S> r, long nq,
+                                                        int Lh, double* partials) {
   __shared__ double red[32];
   typedef typename Store<S>::calc_t C;
-  typedef typename Store<SX>::calc_t CX;
   const C a = (C)(*alpha);
   double acc = 0.0;
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += (long)gridDim.x * blockDim.x) {
-    C pv[4], qv[4], rv[4];
-    CX xv[4];
-    ld_chunk(p, i, Lh, pv);
+    C qv[4], rv[4];
     ld_chunk(q, i, Lh, qv);
-    ld_chunk(CFieldRef<SX>{x.v, x.norm}, i, Lh, xv);
     ld_chunk(CFieldRef<S>{r.v, r.norm}, i, Lh, rv);
     C ps = 0;
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-      xv[e] = fma((CX)a, (CX)pv[e], xv[e]);
       rv[e] = fma(-a, qv[e], rv[e]);
       ps = fma(rv[e], rv[e], ps);
     }
-    st_chunk(x, i, xv);
     st_chunk(r, i, rv);
     acc += (double)ps;
   }
@@ -150,9 +143,8 @@ __global__ void __launch_bounds__(kBlasThreads) k_cg_xr_c(const double* alpha, C
   if (threadIdx.x == 0) partials[blockIdx.x] = t;
 }
 
-__global__ void __launch_bounds__(kBlasThreads) k_cg_xr_p(const double* alpha, CFieldRef<__half> p,
-                                                         CFieldRef<__half> q, FieldRef<float> x, FieldRef<__half> r,
-                                                         long npairs, int Lh, double* partials) {
+__global__ void __launch_bounds__(kBlasThreads) k_cg_r_p(const double* alpha, CFieldRef<__half> q, FieldRef<__half> r,
+                                                        long npairs, int Lh, double* partials) {
   __shared__ double red[32];
   const float a = (float)(*alpha);
   double acc = 0.0;
@@ -164,18 +156,14 @@ __global__ void __launch_bounds__(kBlasThreads) k_cg_xr_p(const double* alpha, C
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
       const long c = (h * 12 + k) * Lh + j;
-      float pv[4], qv[4], rv[4], xv[4];
-      ld_chunk(p, c, Lh, pv);
+      float qv[4], rv[4];
       ld_chunk(q, c, Lh, qv);
-      ld_chunk(CFieldRef<float>{x.v, x.norm}, c, Lh, xv);
       ld_chunk(CFieldRef<__half>{r.v, r.norm}, c, Lh, rv);
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
-        xv[e] = fmaf(a, pv[e], xv[e]);
         rv[e] = fmaf(-a, qv[e], rv[e]);
         ps = fmaf(rv[e], rv[e], ps);
       }
-      st_chunk(x, c, xv);
       re[k] = make_float2(rv[0], rv[1]);
       im[k] = make_float2(rv[2], rv[3]);
     }
@@ -186,25 +174,33 @@ __global__ void __launch_bounds__(kBlasThreads) k_cg_xr_p(const double* alpha, C
   if (threadIdx.x == 0) partials[blockIdx.x] = t;
 }
 
-// ---- p = s + beta p
-template <class S>
-__global__ void __launch_bounds__(kBlasThreads) k_cg_p_c(const double* beta, CFieldRef<S> sv, FieldRef<S> p, long nq,
-                                                        int Lh) {
+// ---- x += alpha p; p = s + beta p   (x may be stored at a higher precision)
+template <class S, class SX>
+__global__ void __launch_bounds__(kBlasThreads) k_cg_xp_c(const double* alpha, const double* beta, CFieldRef<S> sv,
+                                                         FieldRef<S> p, FieldRef<SX> x, long nq, int Lh) {
   typedef typename Store<S>::calc_t C;
-  const C b = (C)(*beta);
+  typedef typename Store<SX>::calc_t CX;
+  const C a = (C)(*alpha), b = (C)(*beta);
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += (long)gridDim.x * blockDim.x) {
-    C a[4], c[4];
-    ld_chunk(sv, i, Lh, a);
-    ld_chunk(CFieldRef<S>{p.v, p.norm}, i, Lh, c);
+    C sw[4], pv[4];
+    CX xv[4];
+    ld_chunk(sv, i, Lh, sw);
+    ld_chunk(CFieldRef<S>{p.v, p.norm}, i, Lh, pv);
+    ld_chunk(CFieldRef<SX>{x.v, x.norm}, i, Lh, xv);
 #pragma unroll
-    for (int e = 0; e < 4; ++e) c[e] = fma(b, c[e], a[e]);
-    st_chunk(p, i, c);
+    for (int e = 0; e < 4; ++e) {
+      xv[e] = fma((CX)a, (CX)pv[e], xv[e]);
+      pv[e] = fma(b, pv[e], sw[e]);
+    }
+    st_chunk(x, i, xv);
+    st_chunk(p, i, pv);
   }
 }
 
-__global__ void __launch_bounds__(kBlasThreads) k_cg_p_p(const double* beta, CFieldRef<__half> sv, FieldRef<__half> p,
-                                                        long npairs, int Lh) {
-  const float b = (float)(*beta);
+__global__ void __launch_bounds__(kBlasThreads) k_cg_xp_p(const double* alpha, const double* beta,
+                                                         CFieldRef<__half> sv, FieldRef<__half> p, FieldRef<float> x,
+                                                         long npairs, int Lh) {
+  const float a = (float)(*alpha), b = (float)(*beta);
   for (long pi = (long)blockIdx.x * blockDim.x + threadIdx.x; pi < npairs; pi += (long)gridDim.x * blockDim.x) {
     const long h = pi / Lh;
     const int j = (int)(pi - h * Lh);
@@ -212,11 +208,15 @@ __global__ void __launch_bounds__(kBlasThreads) k_cg_p_p(const double* beta, CFi
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
       const long c = (h * 12 + k) * Lh + j;
-      float a[4], d[4];
-      ld_chunk(sv, c, Lh, a);
-      ld_chunk(CFieldRef<__half>{p.v, p.norm}, c, Lh, d);
-      re[k] = make_float2(fmaf(b, d[0], a[0]), fmaf(b, d[1], a[1]));
-      im[k] = make_float2(fmaf(b, d[2], a[2]), fmaf(b, d[3], a[3]));
+      float sw[4], pv[4], xv[4];
+      ld_chunk(sv, c, Lh, sw);
+      ld_chunk(CFieldRef<__half>{p.v, p.norm}, c, Lh, pv);
+      ld_chunk(CFieldRef<float>{x.v, x.norm}, c, Lh, xv);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) xv[e] = fmaf(a, pv[e], xv[e]);
+      st_chunk(x, c, xv);
+      re[k] = make_float2(fmaf(b, pv[0], sw[0]), fmaf(b, pv[1], sw[1]));
+      im[k] = make_float2(fmaf(b, pv[2], sw[2]), fmaf(b, pv[3], sw[3]));
     }
     store_pair(p, h, j, Lh, re, im);
   }
@@ -313,42 +313,43 @@ dwf_status blas_copy(dwf_lattice* L, Field x, Field y) { return axpby_any(L, 1.0
 dwf_status blas_zero(dwf_lattice* L, Field x) { return axpby_any(L, 0.0, x, 0.0, x, 0); }
 dwf_status blas_accum(dwf_lattice* L, Field x, Field y) { return axpby_any(L, 1.0, x, 1.0, y, 1); }
 
-dwf_status blas_cg_xr(dwf_lattice* L, const double* alpha, Field p, Field q, Field x, Field r, double* partials,
-                      int* nb) {
+dwf_status blas_cg_r(dwf_lattice* L, const double* alpha, Field q, Field r, double* partials, int* nb) {
   const long nq = nchunks(L), np = npairs(L);
+  if (q.prec != r.prec) return fail(L, DWF_ERR_INVALID_ARG, "cg_r: mixed precisions");
   int g;
-  if (p.prec == DWF_F64 && x.prec == DWF_F64) {
-    g = grid_for(nq);
-    k_cg_xr_c<double, double><<<g, kBlasThreads, 0, L->stream>>>(alpha, cr<double>(p), cr<double>(q), wr<double>(x),
-                                                                  wr<double>(r), nq, L->Lh, partials);
-  } else if (p.prec == DWF_F32 && x.prec == DWF_F32) {
-    g = grid_for(nq);
-    k_cg_xr_c<float, float><<<g, kBlasThreads, 0, L->stream>>>(alpha, cr<float>(p), cr<float>(q), wr<float>(x),
-                                                                wr<float>(r), nq, L->Lh, partials);
-  } else if (p.prec == DWF_F16 && x.prec == DWF_F32) {
-    g = grid_for(np);
-    k_cg_xr_p<<<g, kBlasThreads, 0, L->stream>>>(alpha, cr<__half>(p), cr<__half>(q), wr<float>(x), wr<__half>(r),
-                                                  np, L->Lh, partials);
-  } else {
-    return fail(L, DWF_ERR_INVALID_ARG, "cg_xr: unsupported precision pair");
+  switch (r.prec) {
+    case DWF_F64:
+      g = grid_for(nq);
+      k_cg_r_c<double><<<g, kBlasThreads, 0, L->stream>>>(alpha, cr<double>(q), wr<double>(r), nq, L->Lh, partials);
+      break;
+    case DWF_F32:
+      g = grid_for(nq);
+      k_cg_r_c<float><<<g, kBlasThreads, 0, L->stream>>>(alpha, cr<float>(q), wr<float>(r), nq, L->Lh, partials);
+      break;
+    default:
+      g = grid_for(np);
+      k_cg_r_p<<<g, kBlasThreads, 0, L->stream>>>(alpha, cr<__half>(q), wr<__half>(r), np, L->Lh, partials);
+      break;
   }
   *nb = g;
   DWF_LAUNCHED(L);
   return DWF_OK;
 }
 
-dwf_status blas_cg_p(dwf_lattice* L, const double* beta, Field s, Field p) {
+dwf_status blas_cg_xp(dwf_lattice* L, const double* alpha, const double* beta, Field s, Field p, Field x) {
   const long nq = nchunks(L), np = npairs(L);
-  switch (p.prec) {
-    case DWF_F64:
-      k_cg_p_c<double><<<grid_for(nq), kBlasThreads, 0, L->stream>>>(beta, cr<double>(s), wr<double>(p), nq, L->Lh);
-      break;
-    case DWF_F32:
-      k_cg_p_c<float><<<grid_for(nq), kBlasThreads, 0, L->stream>>>(beta, cr<float>(s), wr<float>(p), nq, L->Lh);
-      break;
-    case DWF_F16:
-      k_cg_p_p<<<grid_for(np), kBlasThreads, 0, L->stream>>>(beta, cr<__half>(s), wr<__half>(p), np, L->Lh);
-      break;
+  if (s.prec != p.prec) return fail(L, DWF_ERR_INVALID_ARG, "cg_xp: mixed precisions");
+  if (p.prec == DWF_F64 && x.prec == DWF_F64) {
+    k_cg_xp_c<double, double><<<grid_for(nq), kBlasThreads, 0, L->stream>>>(alpha, beta, cr<double>(s),
+                                                                             wr<double>(p), wr<double>(x), nq, L->Lh);
+  } else if (p.prec == DWF_F32 && x.prec == DWF_F32) {
+    k_cg_xp_c<float, float><<<grid_for(nq), kBlasThreads, 0, L->stream>>>(alpha, beta, cr<float>(s), wr<float>(p),
+                                                                           wr<float>(x), nq, L->Lh);
+  } else if (p.prec == DWF_F16 && x.prec == DWF_F32) {
+    k_cg_xp_p<<<grid_for(np), kBlasThreads, 0, L->stream>>>(alpha, beta, cr<__half>(s), wr<__half>(p), wr<float>(x),
+                                                             np, L->Lh);
+  } else {
+    return fail(L, DWF_ERR_INVALID_ARG, "cg_xp: unsupported precision pair");
   }
   DWF_LAUNCHED(L);
   return DWF_OK;

@@ -361,6 +361,19 @@ dwf_status launch_hop_batch(dwf_lattice* L, const HopCall& c, const HopBatch& b,
 // largest batch a single launch takes at this Ls and precision (0: none)
 int hop_batch_max(int Ls, dwf_prec prec);
 
+// cg.cu: the even-odd solve of D(m) x = b on FP64 parity fields (xe holds the
+// guess).  zero_guess: xe is known to be zero (skips the FP64 residual of the
+// guess); full_check = false: report the CG residual |b' - M~ x~| / |b| (equal
+// to the full one up to rounding) instead of recomputing |b - D x| in FP64.
+struct SolveOpts {
+  bool zero_guess = false;
+  bool full_check = true;
+};
+dwf_status solve_eo(dwf_lattice* L, double m, Field be, Field bo, Field xe, Field xo, const dwf_cg_params& prm,
+                    dwf_stats* st, double* true_res_full, const SolveOpts& opts = SolveOpts());
+// lattice.cu: out_e/out_o = D(m) x or D(m)^+ x on FP64 fields
+dwf_status apply_D(dwf_lattice* L, const SOps* ops, bool dag, Field xe, Field xo, Field oe, Field oo);
+
 // tune.cu: launch-shape autotuner for batched hops
 struct HopShape {
   long Vh;
@@ -396,9 +409,10 @@ dwf_status blas_zero(dwf_lattice* L, Field x);
 // y = a*x + b*y with host scalars (any precisions)
 dwf_status blas_axpby(dwf_lattice* L, double a, Field x, double b, Field y);
 // CG steps with device scalars (pointers into L->scal)
-dwf_status blas_cg_xr(dwf_lattice* L, const double* alpha, Field p, Field q, Field x, Field r,
-                      double* partials, int* nb);  // x += a p; r -= a q; |r|^2
-dwf_status blas_cg_p(dwf_lattice* L, const double* beta, Field s, Field p);  // p = s + b p
+// r -= alpha q with partial sums of |r|^2 (q, r same precision)
+dwf_status blas_cg_r(dwf_lattice* L, const double* alpha, Field q, Field r, double* partials, int* nb);
+// x += alpha p; p = s + beta p  (the solution moves with the old direction in the same pass)
+dwf_status blas_cg_xp(dwf_lattice* L, const double* alpha, const double* beta, Field s, Field p, Field x);
 // add a lower-precision field into another: y += x
 dwf_status blas_accum(dwf_lattice* L, Field x, Field y);
 // scalar kernels

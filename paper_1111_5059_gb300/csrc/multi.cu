@@ -24,9 +24,6 @@
 
 namespace dwf {
 
-dwf_status apply_D(dwf_lattice* L, const SOps* ops, bool dag, Field xe, Field xo, Field oe, Field oo);
-dwf_status solve_eo(dwf_lattice* L, double m, Field be, Field bo, Field xe, Field xo, const dwf_cg_params& prm,
-                    dwf_stats* st, double* true_res_full);
 
 namespace {
 
@@ -212,7 +209,7 @@ dwf_status iterate(Multi& M, const std::vector<int>& set) {
   }
   for (int i = 0; i < k; ++i) {
     Rhs& R = M.R[set[i]];
-    DWF_TRY(blas_cg_xr(L, M.sc(set[i], M_ALPHA), R.p, R.q, R.x, R.r, pr[i], &R.nr));
+    DWF_TRY(blas_cg_r(L, M.sc(set[i], M_ALPHA), R.q, R.r, pr[i], &R.nr));
   }
   DWF_TRY(apply_Mt_set(M, set, true, Rr.data(), S.data(), U.data(), ps.data(), ns.data()));
   for (int i = 0; i < k; ++i) {
@@ -221,7 +218,7 @@ dwf_status iterate(Multi& M, const std::vector<int>& set) {
   }
   for (int i = 0; i < k; ++i) {
     Rhs& R = M.R[set[i]];
-    DWF_TRY(blas_cg_p(L, M.sc(set[i], M_BETA), R.s, R.p));
+    DWF_TRY(blas_cg_xp(L, M.sc(set[i], M_ALPHA), M.sc(set[i], M_BETA), R.s, R.p, R.x));
   }
   return DWF_OK;
 }

@@ -1,0 +1,64 @@
+"""Pins from parameters the paper prints (tests/golden/mobius_params_fig1_table1.txt).
+
+The paper gives no worked numerical example; what it does print are the
+MADWF parameters of Fig. 1 and Table 1 (Sec. 5).  They pin the reading used
+for the Moebius intermediate -- b - c = 1 and b + c = L / L' -- and the
+benchmark's defect-correction settings.
+"""
+import os
+import sys
+
+import numpy as np
+
+from oracle import dwf_oracle as O
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def _golden():
+    g = {}
+    with open(os.path.join(HERE, "golden", "mobius_params_fig1_table1.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                tag, key, val = line.split()
+                g[(tag, key)] = float(val)
+    return g
+
+
+def _rule(L, Lp):
+    """b - c = 1, b + c = L / L'."""
+    s = L / Lp
+    return (s + 1) / 2, (s - 1) / 2
+
+
+def test_fig1_parameters_follow_the_reading():
+    g = _golden()
+    b, c = _rule(g[("fig1", "L")], g[("fig1", "Lp")])
+    assert (b, c) == (g[("fig1", "b")], g[("fig1", "c")])
+
+
+def test_scaled_kernel_matches_sign_function_at_small_lambda():
+    # With b - c = 1 the Moebius kernel is (b + c) times the Shamir one, and
+    # eps_L'((L/L') lam) agrees with eps_L(lam) to O(lam^3): the reading's
+    # purpose, checked on the oracle's polar approximation with Fig. 1's L, L'.
+    g = _golden()
+    L, Lp = int(g[("fig1", "L")]), int(g[("fig1", "Lp")])
+    lam = np.diag([1e-3, 3e-3, -2e-3, 1e-2])
+    e_L = np.diag(O.eps_L(lam, L))
+    e_Lp = np.diag(O.eps_L((L / Lp) * lam, Lp))
+    assert np.allclose(e_L, e_Lp, rtol=0, atol=5e-3)
+    # a wrong scale (b + c = 1, the unscaled Moebius) misses by O(1) there
+    e_wrong = np.diag(O.eps_L(lam, Lp))
+    assert np.abs(e_wrong - e_L).max() > 0.05
+
+
+def test_benchmark_madwf_settings_follow_table1():
+    g = _golden()
+    sys.path.insert(0, os.path.dirname(HERE))
+    import bench
+
+    w = bench.WORKLOADS["madwf"]
+    assert w["Ls"] == g[("table1", "L")] and w["inner_Ls"] == g[("table1", "Lp")]
+    assert w["n_dc"] == g[("table1", "n_dc")]
+    b, c = _rule(w["Ls"], w["inner_Ls"])
+    assert abs(w["b"] - b) < 1e-15 and abs(w["c"] - c) < 1e-15

@@ -154,3 +154,40 @@ def test_full_ladder_size_sampled_residuals(dwf):
         assert np.abs(got - want).max() <= 1e-10 * bnorm
         del x
     lat.close()
+
+
+_TUNE_SCRIPT = r"""
+import json, sys, torch
+sys.path.insert(0, {root!r})
+from paper_1111_5059_gb300 import dwf, inputs
+dims, Ls = (4, 4, 4, 8), 8
+lat = dwf.Lattice(dims, Ls, 1.8, 1.5, 0.5)
+lat.set_gauge(torch.from_numpy(inputs.gauge_field(5, dims, 0.6)).cuda())
+bs = [torch.from_numpy(inputs.gaussian_spinor(10 + r, dims, Ls)).cuda() for r in range(3)]
+xs, st, info, status = lat.cg_multi((0.01, 0.05, 0.2), bs, inner="f32", autotune=True)
+print(json.dumps({{"status": status, "tune_seconds": info["tune_seconds"], "batch": info["batch"]}}))
+"""
+
+
+def test_autotune_cache_file_is_written_and_reused(dwf, tmp_path):
+    """DWF_TUNE_CACHE: the first process times the candidates and appends the
+    winners; a second process reads them back and tunes nothing."""
+    import json
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    cache = tmp_path / "tune.txt"
+    env = dict(os.environ, DWF_TUNE_CACHE=str(cache))
+    script = _TUNE_SCRIPT.format(root=root)
+    out = []
+    for _ in range(2):
+        r = subprocess.run([sys.executable, "-c", script], capture_output=True, text=True, env=env, timeout=600)
+        assert r.returncode == 0, r.stderr
+        out.append(json.loads(r.stdout.strip().splitlines()[-1]))
+    lines = cache.read_text().strip().splitlines()
+    assert len(lines) >= 2 and all(len(l.split()) == 4 for l in lines)
+    assert out[0]["status"] == 0 and out[1]["status"] == 0
+    assert out[0]["tune_seconds"] > 0.0 and out[1]["tune_seconds"] == 0.0
+    assert out[0]["batch"] == out[1]["batch"]

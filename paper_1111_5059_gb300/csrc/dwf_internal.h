@@ -2,13 +2,15 @@
 //
 // Internal layouts (one checkerboard, "half" lattice of Vh = V4/2 sites):
 //   spinor  : the Ls slices of a 4D site are split into Lh = ceil(Ls/2) pairs
-//             (j, j + Lh).  Element order [h][k][j][4] with the 4 elements
-//             (re s0, re s1, im s0, im s1), s0 = j, s1 = j + Lh, complex
-//             component k = spin * 3 + colour (spins 0,1 = P+ half).  One
-//             16-byte FP32 chunk therefore holds one complex component of two
-//             slices, so a thread owning the pair (h, j) computes both slices
-//             with packed FP32x2 instructions, and the Ls / 2 threads of a
-//             site read consecutive chunks.  All precisions share the element
+//             of neighbouring slices (2j, 2j + 1).  Element order [h][k][j][4]
+//             with the 4 elements (re s0, re s1, im s0, im s1), s0 = 2j,
+//             s1 = 2j + 1, complex component k = spin * 3 + colour (spins 0,1
+//             = P+ half).  One 16-byte FP32 chunk therefore holds one complex
+//             component of two slices, so a thread owning the pair (h, j)
+//             computes both slices with packed FP32x2 instructions, the Ls / 2
+//             threads of a site read consecutive chunks, and the slice
+//             recurrences of the fifth-dimension operators pass one value
+//             between neighbouring threads.  All precisions share the element
 //             order (FP64: 32-byte chunks; FP16: 8-byte chunks plus one FP32
 //             scale per (h, slice), stored [h][j][2]), so precision casts and
 //             level-1 kernels are flat element-wise loops.  For odd Ls the
@@ -75,8 +77,8 @@ template <class S>
 __device__ __forceinline__ void load_spinor(CFieldRef<S> f, long h, int s, int Lh,
                                             typename Store<S>::calc_t* v) {
   typedef typename Store<S>::calc_t C;
-  const int half = s >= Lh ? 1 : 0;
-  const int j = s - half * Lh;
+  const int half = s & 1;
+  const int j = s >> 1;
   const S* base = f.v + elem_index(h, 0, j, Lh) + half;
   C sc = 1;
   if constexpr (sizeof(S) == 2) sc = __ldg(f.norm + ((long)h * Lh + j) * 2 + half);
@@ -98,8 +100,8 @@ __device__ __forceinline__ float half_scale(float mx, float* inv) {
 template <class S>
 __device__ __forceinline__ void store_spinor(FieldRef<S> f, long h, int s, int Lh,
                                              const typename Store<S>::calc_t* v) {
-  const int half = s >= Lh ? 1 : 0;
-  const int j = s - half * Lh;
+  const int half = s & 1;
+  const int j = s >> 1;
   S* base = f.v + elem_index(h, 0, j, Lh) + half;
   if constexpr (sizeof(S) == 2) {
     float mx = 0.f;

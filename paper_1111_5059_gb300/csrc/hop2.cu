@@ -8,7 +8,7 @@
 // with the fifth-dimension operators of the even-odd Schur form fused).
 //
 // GB300 design:
-//  * Thread (i, r, j) owns the slice pair (j, j + Lh) of 4D site i of
+//  * Thread (i, r, j) owns the slice pair (2j, 2j + 1) of 4D site i of
 //    right-hand side r, so both lanes of every packed FP32x2 FMA
 //    (__ffma2_rn) use the same link element.  One launch may cover up to
 //    kMaxBatch right-hand sides (a mass ladder) that share the links.
@@ -155,25 +155,25 @@ __device__ __forceinline__ void hop_dir2(float sg, const float2* pr, const float
 // bytes of one complex-component chunk of a slice pair
 template <class S> __host__ __device__ constexpr int chunk_bytes() { return sizeof(S) == 4 ? 16 : 8; }
 
-// Write the pair (re, im) of slices j, j + Lh of tile block bi into the s-op tile.
+// Write the pair (re, im) of slices 2j, 2j + 1 of tile block bi into the s-op tile.
 __device__ __forceinline__ void tile_put_pair(float* tile, int R, int bi, int j, int Lh, int Ls, const float2* re,
                                               const float2* im) {
   float* base = tile + (bi * 12) * R;
-  const bool two = j + Lh < Ls;
+  const bool two = 2 * j + 1 < Ls;
 #pragma unroll
   for (int k = 0; k < 12; ++k) {
-    reinterpret_cast<float2*>(base + k * R)[j] = make_float2(re[k].x, im[k].x);
-    if (two) reinterpret_cast<float2*>(base + k * R)[j + Lh] = make_float2(re[k].y, im[k].y);
+    reinterpret_cast<float2*>(base + k * R)[2 * j] = make_float2(re[k].x, im[k].x);
+    if (two) reinterpret_cast<float2*>(base + k * R)[2 * j + 1] = make_float2(re[k].y, im[k].y);
   }
 }
 __device__ __forceinline__ void tile_get_pair(const float* tile, int R, int bi, int j, int Lh, int Ls, float2* re,
                                               float2* im) {
   const float* base = tile + (bi * 12) * R;
-  const bool two = j + Lh < Ls;
+  const bool two = 2 * j + 1 < Ls;
 #pragma unroll
   for (int k = 0; k < 12; ++k) {
-    const float2 a = reinterpret_cast<const float2*>(base + k * R)[j];
-    const float2 b = two ? reinterpret_cast<const float2*>(base + k * R)[j + Lh] : make_float2(0.f, 0.f);
+    const float2 a = reinterpret_cast<const float2*>(base + k * R)[2 * j];
+    const float2 b = two ? reinterpret_cast<const float2*>(base + k * R)[2 * j + 1] : make_float2(0.f, 0.f);
     re[k] = make_float2(a.x, b.x);
     im[k] = make_float2(a.y, b.y);
   }
@@ -190,100 +190,118 @@ template <class T> __device__ __forceinline__ T pick(const T* arr, int r) {
 
 // y <- op y on the slice pairs a lane holds, for a structured operator and
 // even Ls >= 2, without shared memory: the Ls slices of a site live in its Lh
-// lanes base .. base + Lh - 1 (slice j in .x, slice j + Lh in .y of lane
-// base + j).  With u = x / g2, the inverse (g2 + d2 Q)^-1 is the first-order
-// recurrence z_s = rho z_{s-1} + u_s closed by the wall term -m: a log-depth
-// scan across the lanes gives the open prefix P_s, the two halves are joined
-// by P_{Lh-1}, and the wall adds rho^s w with w = -rho m P_{Ls-1} / (1 + m rho^Ls).
-// Rows that walk down in s (P- rows, or P+ rows of a transposed operator) use
-// the mirrored suffix form.  y = g1 z + d1 Q z then needs one neighbouring
-// slice, one shuffle away.
+// lanes base .. base + Lh - 1, slice 2j in .x and 2j + 1 in .y of lane
+// base + j.  With u = x / g2, the inverse (g2 + d2 Q)^-1 is the first-order
+// recurrence z_s = rho z_{s-1} + u_s closed by the wall term -m: each lane
+// first folds its own two slices, a log-depth scan across the lanes (factor
+// rho^2 per lane) gives the open prefix P at every odd slice, one more
+// neighbour value gives it at the even ones, and the wall adds rho^s w with
+// w = -rho m P_{Ls-1} / (1 + m rho^Ls).  Rows that walk down in s (P- rows,
+// or P+ rows of a transposed operator) use the mirrored suffix form.
+// y = g1 z + d1 Q z then needs one neighbouring slice, at most one shuffle
+// away.  The (re, im) pair of a slice moves as one float2.
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 
+__device__ __forceinline__ float2 shfl2(float2 v, int src) {
+  return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+
 __device__ __forceinline__ void sop_shfl(const SOpK<float>& op, float2* re, float2* im, int j, int Lh) {
-  constexpr unsigned F = 0xffffffffu;
   const int lane = threadIdx.x, base = lane - j;
   const float rho = op.rho, m = op.m;
-  // lane powers of rho: rho^j, rho^Lh, rho^(Lh-j), rho^(Lh-1-j)
-  float pj = 1.f, pL = 1.f, pLj = 1.f, pLj1 = 1.f;
+  // lane powers of rho: rho^(2j), rho^(Ls-1-2j) (Ls = 2 Lh)
+  float p2j = 1.f, pr2j = 1.f;
   if (op.has_inv)
     for (int q = 0; q < Lh; ++q) {
-      pL *= rho;
-      if (q < j) pj *= rho;
-      if (q >= j) pLj *= rho;
-      if (q > j) pLj1 *= rho;
+      if (q < j) p2j *= rho * rho;
+      if (q > j) pr2j *= rho * rho;
     }
   const float wk = op.has_inv ? -rho * m * (op.c0 / op.ginv) : 0.f;  // -rho m / (1 + m rho^Ls)
 #pragma unroll
   for (int half = 0; half < 2; ++half) {
     const int up = half ^ op.trans;  // 0: z_s from z_{s-1} (prefix); 1: from z_{s+1} (suffix)
-    float2* R = re + 6 * half;
-    float2* I = im + 6 * half;
+    // per component k: a = slice 2j, b = slice 2j + 1, each (re, im)
+    float2 A[6], B[6];
     const float2 gi = f2(op.ginv);
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
-      R[k] = mul2(gi, R[k]);
-      I[k] = mul2(gi, I[k]);
+      const int kk = 6 * half + k;
+      A[k] = mul2(gi, make_float2(re[kk].x, im[kk].x));
+      B[k] = mul2(gi, make_float2(re[kk].y, im[kk].y));
     }
     if (op.has_inv) {
-      float rd = rho;
-      for (int d = 1; d < Lh; d <<= 1) {
-        const bool ok = up ? (j + d < Lh) : (j >= d);
-        const int src = ok ? (up ? lane + d : lane - d) : lane;
-        const float2 f = f2(ok ? rd : 0.f);
-#pragma unroll
-        for (int k = 0; k < 6; ++k) {
-          const float2 tr = make_float2(__shfl_sync(F, R[k].x, src), __shfl_sync(F, R[k].y, src));
-          const float2 ti = make_float2(__shfl_sync(F, I[k].x, src), __shfl_sync(F, I[k].y, src));
-          R[k] = fma2(f, tr, R[k]);
-          I[k] = fma2(f, ti, I[k]);
-        }
-        rd *= rd;
-      }
+      const float2 r1 = f2(rho);
       if (!up) {
-        // second half += rho^(j+1) P_{Lh-1}; then the wall, P_{Ls-1} in .y of the last lane
-        const float cf = pj * rho;
-        const float2 ps = make_float2(pj, pj * pL);
+        // fold the lane's two slices, scan the odd-slice values across lanes
 #pragma unroll
-        for (int k = 0; k < 6; ++k) {
-          R[k].y = fmaf(cf, __shfl_sync(F, R[k].x, base + Lh - 1), R[k].y);
-          I[k].y = fmaf(cf, __shfl_sync(F, I[k].x, base + Lh - 1), I[k].y);
+        for (int k = 0; k < 6; ++k) B[k] = fma2(r1, A[k], B[k]);
+        float rd = rho * rho;
+        for (int d = 1; d < Lh; d <<= 1) {
+          const bool ok = j >= d;
+          const int src = ok ? lane - d : lane;
+          const float2 f = f2(ok ? rd : 0.f);
+#pragma unroll
+          for (int k = 0; k < 6; ++k) B[k] = fma2(f, shfl2(B[k], src), B[k]);
+          rd *= rd;
         }
+        // even slices: P_{2j} = u_{2j} + rho P_{2j-1}; then the wall, P_{Ls-1} in .y of the last lane
+        const int src = j > 0 ? lane - 1 : lane;
+        const float2 f = f2(j > 0 ? rho : 0.f);
+        const float2 ps = make_float2(p2j, p2j * rho);
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
-          R[k] = fma2(ps, f2(wk * __shfl_sync(F, R[k].y, base + Lh - 1)), R[k]);
-          I[k] = fma2(ps, f2(wk * __shfl_sync(F, I[k].y, base + Lh - 1)), I[k]);
+          A[k] = fma2(f, shfl2(B[k], src), A[k]);
+          const float2 w = mul2(f2(wk), shfl2(B[k], base + Lh - 1));
+          A[k] = fma2(f2(ps.x), w, A[k]);
+          B[k] = fma2(f2(ps.y), w, B[k]);
         }
       } else {
-        // first half += rho^(Lh-j) S_{Lh}; then the wall, S_0 in .x of the first lane
-        const float2 ps = make_float2(pLj1 * pL, pLj1);
+        // mirrored: fold from the right, scan the even-slice values across lanes
 #pragma unroll
-        for (int k = 0; k < 6; ++k) {
-          R[k].x = fmaf(pLj, __shfl_sync(F, R[k].y, base), R[k].x);
-          I[k].x = fmaf(pLj, __shfl_sync(F, I[k].y, base), I[k].x);
+        for (int k = 0; k < 6; ++k) A[k] = fma2(r1, B[k], A[k]);
+        float rd = rho * rho;
+        for (int d = 1; d < Lh; d <<= 1) {
+          const bool ok = j + d < Lh;
+          const int src = ok ? lane + d : lane;
+          const float2 f = f2(ok ? rd : 0.f);
+#pragma unroll
+          for (int k = 0; k < 6; ++k) A[k] = fma2(f, shfl2(A[k], src), A[k]);
+          rd *= rd;
         }
+        // odd slices: S_{2j+1} = u_{2j+1} + rho S_{2j+2}; then the wall, S_0 in .x of the first lane
+        const int src = j < Lh - 1 ? lane + 1 : lane;
+        const float2 f = f2(j < Lh - 1 ? rho : 0.f);
+        const float2 ps = make_float2(pr2j * rho, pr2j);  // rho^(Ls-1-2j), rho^(Ls-2-2j)
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
-          R[k] = fma2(ps, f2(wk * __shfl_sync(F, R[k].x, base)), R[k]);
-          I[k] = fma2(ps, f2(wk * __shfl_sync(F, I[k].x, base)), I[k]);
+          B[k] = fma2(f, shfl2(A[k], src), B[k]);
+          const float2 w = mul2(f2(wk), shfl2(A[k], base));
+          A[k] = fma2(f2(ps.x), w, A[k]);
+          B[k] = fma2(f2(ps.y), w, B[k]);
         }
       }
     }
-    // y = g1 z + d1 Q z: the neighbouring slice, or -m times the other wall
+    // y = g1 z + d1 Q z: the neighbouring slice (in this lane or the next /
+    // previous one), or -m times the slice at the other wall
+    const float2 g1 = f2(op.g1), d1 = f2(op.d1);
     const bool edge = up ? (j == Lh - 1) : (j == 0);
     const int src = up ? (edge ? base : lane + 1) : (edge ? base + Lh - 1 : lane - 1);
-    const float2 g1 = f2(op.g1), d1 = f2(op.d1);
+    const float2 fe = f2(edge ? -m : 1.f);
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
-      const float ar = __shfl_sync(F, R[k].x, src), br = __shfl_sync(F, R[k].y, src);
-      const float ai = __shfl_sync(F, I[k].x, src), bi = __shfl_sync(F, I[k].y, src);
-      float2 qr = make_float2(ar, br), qi = make_float2(ai, bi);
-      if (edge) {
-        qr = up ? make_float2(br, -m * ar) : make_float2(-m * br, ar);
-        qi = up ? make_float2(bi, -m * ai) : make_float2(-m * bi, ai);
+      const int kk = 6 * half + k;
+      float2 ya, yb;
+      if (!up) {
+        const float2 q = mul2(fe, shfl2(B[k], src));  // slice 2j-1 (or -m slice Ls-1)
+        ya = fma2(d1, q, mul2(g1, A[k]));
+        yb = fma2(d1, A[k], mul2(g1, B[k]));
+      } else {
+        const float2 q = mul2(fe, shfl2(A[k], src));  // slice 2j+2 (or -m slice 0)
+        ya = fma2(d1, B[k], mul2(g1, A[k]));
+        yb = fma2(d1, q, mul2(g1, B[k]));
       }
-      R[k] = fma2(d1, qr, mul2(g1, R[k]));
-      I[k] = fma2(d1, qi, mul2(g1, I[k]));
+      re[kk] = make_float2(ya.x, yb.x);
+      im[kk] = make_float2(ya.y, yb.y);
     }
   }
 }
@@ -317,7 +335,7 @@ __device__ __forceinline__ void sop_pair(const SOpK<float>* ops, float2* re, flo
       re[k] = make_float2(0.f, 0.f);
       im[k] = re[k];
     }
-    const int s0 = j, s1 = j + Lh < Ls ? j + Lh : j;
+    const int s0 = 2 * j, s1 = 2 * j + 1 < Ls ? 2 * j + 1 : 2 * j;
     for (int t = 0; t < Ls; ++t) {
       const float e0p = op.dense[s0 * Ls + t], e0m = op.dense[Ls * Ls + s0 * Ls + t];
       const float e1p = op.dense[s1 * Ls + t], e1m = op.dense[Ls * Ls + s1 * Ls + t];
@@ -329,7 +347,7 @@ __device__ __forceinline__ void sop_pair(const SOpK<float>* ops, float2* re, flo
         im[k] = fma2(e, f2(v.y), im[k]);
       }
     }
-    if (!(j + Lh < Ls))
+    if (!(2 * j + 1 < Ls))
 #pragma unroll
       for (int k = 0; k < 12; ++k) {
         re[k].y = 0.f;
@@ -625,7 +643,7 @@ __global__ void __launch_bounds__(32, 12) hop3_kernel(const Hop3Args<S> a) {
                Ls, Lh);
     // the delayed refill of the tile's slot: the next group's stage kSlots - 1
     issue_stage<S>(P, g + stride, kSlots - 1, tslot, lb ^ 1);
-    if (j + Lh >= Ls) {  // odd Ls: the padding slot stays zero
+    if (2 * j + 1 >= Ls) {  // odd Ls: the padding slot stays zero
 #pragma unroll
       for (int k = 0; k < 12; ++k) {
         ar[k].y = 0.f;

@@ -214,6 +214,11 @@ typedef struct {
 dwf_status dwf_force(dwf_lattice_t h, int nterms, const dwf_quotient* terms, const void* const* phi,
                      void* const* X_io, void* F, void* G, double* S, const dwf_cg_params* cg, dwf_stats* stats);
 
+/* The action alone: S (host double, required) = sum over the terms of
+ * |M1 (M1^+ M1)^-1 M2^+ phi|^2, as dwf_force computes it with F = G = NULL. */
+dwf_status dwf_action(dwf_lattice_t h, int nterms, const dwf_quotient* terms, const void* const* phi,
+                      const dwf_cg_params* cg, double* S);
+
 /* The force-gradient link update (Sec. 2, Eq. for U'): for every link,
  * U_out = exp(coeff * sum_j X^j T_j) U_in with X float64 [4][T][Z][Y][X][8]
  * and U complex128 boundary layout (U_out may equal U_in).  coeff =

@@ -572,3 +572,9 @@ dwf_status dwf_kinetic(dwf_lattice_t L, const void* p, double* T) {
 }
 
 }  // extern "C"
+
+extern "C" dwf_status dwf_action(dwf_lattice_t L, int nterms, const dwf_quotient* terms, const void* const* phi,
+                                 const dwf_cg_params* prm, double* S) {
+  if (!S) return fail(L, DWF_ERR_INVALID_ARG, "dwf_action: null result pointer");
+  return dwf_force(L, nterms, terms, phi, nullptr, nullptr, nullptr, S, prm, nullptr);
+}

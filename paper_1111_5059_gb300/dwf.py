@@ -109,6 +109,8 @@ def _declare(lib):
         "dwf_apply_Mpc_noalloc": [H, ctypes.c_double, ctypes.c_int, _VP, _VP],
         "dwf_force": [H, ctypes.c_int, ctypes.POINTER(Quotient), ctypes.POINTER(_VP), ctypes.POINTER(_VP), _VP, _VP,
                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(CGParams), ctypes.POINTER(Stats)],
+        "dwf_action": [H, ctypes.c_int, ctypes.POINTER(Quotient), ctypes.POINTER(_VP), ctypes.POINTER(CGParams),
+                       ctypes.POINTER(ctypes.c_double)],
         "fgi_link_update": [H, _VP, ctypes.c_double, _VP, _VP],
         "dwf_momentum_update": [H, _VP, ctypes.c_double, _VP],
         "dwf_kinetic": [H, _VP, ctypes.POINTER(ctypes.c_double)],
@@ -326,6 +328,16 @@ def force(lat: Lattice, terms, phis, want_force=True, want_grad=False, X_io=None
               _VP(_ptr(F, dtype=torch.float64)) if F is not None else _VP(),
               _VP(_ptr(G)) if G is not None else _VP(), ctypes.byref(S), ctypes.byref(prm), ctypes.byref(st))
     return S.value, F, G, st.as_dict()
+
+
+def action_value(lat: Lattice, terms, phis, tol=1e-12, inner="f64", max_iter=100000, delta=0.1,
+                 check_every=10) -> float:
+    """The quotient action alone (see include/dwf.h, dwf_action)."""
+    S = ctypes.c_double()
+    prm = CGParams(float(tol), int(max_iter), _PREC[inner], float(delta), int(check_every))
+    lat._call(lib().dwf_action, len(terms), _terms(terms), _ptr_array(phis, lat.spinor_shape), ctypes.byref(prm),
+              ctypes.byref(S))
+    return S.value
 
 
 def fgi_link_update(lat: Lattice, X: torch.Tensor, coeff: float, U_in: torch.Tensor, U_out=None) -> torch.Tensor:

@@ -51,6 +51,8 @@ def test_action_and_force_match_oracle(small, dwf):
     S, F, _, st = dwf.force(lat, TERMS, [_to(x) for x in phis], tol=1e-13)
     So, Fo, _ = O.action_and_force(U, phis, TERMS, M5, tol=1e-14)
     assert abs(S - So) / So < 1e-11
+    # the action-only entry point runs the same solves
+    assert abs(dwf.action_value(lat, TERMS, [_to(x) for x in phis], tol=1e-13) - S) <= 1e-14 * abs(S)
     Fg = F.cpu().numpy()
     assert np.abs(Fg - Fo).max() / np.abs(Fo).max() < 1e-9
     assert st["iters"] > 0

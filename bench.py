@@ -335,6 +335,16 @@ def run_ladder(args, w, inner, world, rank, local, dev, hbm_peak, peak_src):
         del bd, xs
     e2e_ms = max_over_ranks(world, statistics.mean(e2e), dev)
 
+    # ---- the same ladder with every right-hand side in one hop launch (no autotuning)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    _, _, info_all, _ = lat.cg_multi(masses, bs, tol=args.tol, inner=inner, delta=DELTA, check_every=10,
+                                     autotune=False)
+    e1.record(stream)
+    e1.synchronize()
+    one_launch = {"seconds": e0.elapsed_time(e1) / 1e3, "batch": info_all["batch"]}
+
     # ---- the same four solves one after the other (single-RHS mixed CG)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -371,7 +381,8 @@ def run_ladder(args, w, inner, world, rank, local, dev, hbm_peak, peak_src):
             "e2e": {"value": e2e_ms / 1e3 / world, "unit": "s",
                     "h2d_bytes_per_step": sum(h.numel() * 16 for h in b_host),
                     "d2h_bytes_per_step": sum(h.numel() * 16 for h in x_host)},
-            "gpu_launches": launches, "solve": solve_info, "sequential_cg": sequential, "clocks": clk.summary()}
+            "gpu_launches": launches, "solve": solve_info, "sequential_cg": sequential,
+            "all_rhs_one_launch": one_launch, "clocks": clk.summary()}
     if rank == 0:
         if not args.no_cpu_baseline:
             iters = sum(s["iters"] for s in st)

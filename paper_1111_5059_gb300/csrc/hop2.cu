@@ -8,22 +8,22 @@
 // with the fifth-dimension operators of the even-odd Schur form fused).
 //
 // GB300 design:
-//  * Thread (i, r, j) owns the slice pair (2j, 2j + 1) of 4D site i of
-//    right-hand side r, so both lanes of every packed FP32x2 FMA
-//    (__ffma2_rn) use the same link element.  One launch may cover up to
-//    kMaxBatch right-hand sides (a mass ladder) that share the links.
-//  * A CTA is one warp that walks a stream of site groups (G sites of every
-//    right-hand side per group, G * nr * Lh <= 32).  A group is a sequence
-//    of stages: the 8 directions (the neighbour blocks of that direction --
-//    a neighbour's 5D spinor block is contiguous in the pair layout, and the
-//    neighbours of consecutive sites are usually consecutive, so a stage is
-//    one bulk copy per right-hand side; stage 0 also brings the group's
-//    links) and, if the hop has a site term, the group's own blocks.  Stages
-//    are fetched by the bulk copy engine (cp.async.bulk, completion counted
-//    on an mbarrier per slot) into a ring of kSlots shared-memory slots in
-//    issue order, across group boundaries; no block barrier exists.  Two
-//    slots (one stage in flight per warp) leave room for more resident warps,
-//    which measured faster than deeper rings.
+//  * Thread (i, j) owns the slice pair (2j, 2j + 1) of 4D site i, so both
+//    lanes of every packed FP32x2 FMA (__ffma2_rn) use the same link element.
+//  * A CTA is one warp that walks a stream of site groups (G = 32 / Lh
+//    consecutive sites per group).  A group is a sequence of stages: the 8
+//    directions (the neighbour blocks of that direction -- a neighbour's 5D
+//    spinor block is contiguous in the pair layout, and the neighbours of
+//    consecutive sites are usually consecutive, so a stage is one bulk copy;
+//    stage 0 also brings the group's links) and, if the hop has a site term,
+//    the group's own blocks.  A launch over several right-hand sides (a mass
+//    ladder) runs these stages for each of them in turn, so a group's links
+//    and neighbour indices are staged once for all of them.  Stages are
+//    fetched by the bulk copy engine (cp.async.bulk, completion counted on an
+//    mbarrier per slot) into a ring of kSlots shared-memory slots in issue
+//    order, across group boundaries; no block barrier exists.  Two slots (one
+//    stage in flight per warp) leave room for more resident warps, which
+//    measured faster than deeper rings.
 //  * Links are read once per group from shared memory and reused over all Ls
 //    slices (and right-hand sides).
 //  * The fifth-dimension epilogue stays in registers for even Ls: the s
@@ -179,15 +179,6 @@ __device__ __forceinline__ void tile_get_pair(const float* tile, int R, int bi, 
   }
 }
 
-// arr[r] for a runtime r < kMaxBatch, by selects (arr lives in kernel parameter space)
-template <class T> __device__ __forceinline__ T pick(const T* arr, int r) {
-  T v = arr[0];
-#pragma unroll
-  for (int q = 1; q < kMaxBatch; ++q)
-    if (r == q) v = arr[q];
-  return v;
-}
-
 // y <- op y on the slice pairs a lane holds, for a structured operator and
 // even Ls >= 2, without shared memory: the Ls slices of a site live in its Lh
 // lanes base .. base + Lh - 1, slice 2j in .x and 2j + 1 in .y of lane
@@ -306,29 +297,24 @@ __device__ __forceinline__ void sop_shfl(const SOpK<float>& op, float2* re, floa
   }
 }
 
-// (re, im) <- ops[r] (re, im) across the warp, through the tile (all lanes
-// call).  Tile block bi = r * G + i holds site i of right-hand side r; all
-// right-hand sides of a launch share the operator kind.
-template <int NRC>
-__device__ __forceinline__ void sop_pair(const SOpK<float>* ops, float2* re, float2* im, float* tile, int bi, int r,
-                                         int j, bool act, int G, int nact, int nr, int Ls, int Lh) {
-  if (ops[0].kind == 1 && !(Ls & 1)) {  // registers and shuffles only (every lane calls)
-    sop_shfl(pick(ops, NRC == 1 ? 0 : r), re, im, j, Lh);
+// (re, im) <- op (re, im) for slot block bi, pair j (every lane calls): in
+// registers for a structured operator and even Ls, otherwise through the
+// shared-memory tile (the slot just consumed).
+__device__ __forceinline__ void sop_pair(const SOpK<float>& op, float2* re, float2* im, float* tile, int bi, int j,
+                                         bool act, int G, int nact, int Ls, int Lh) {
+  if (op.kind == 1 && !(Ls & 1)) {
+    sop_shfl(op, re, im, j, Lh);
     return;
   }
   const int R = tile_row(Ls);
   if (act) tile_put_pair(tile, R, bi, j, Lh, Ls, re, im);
   __syncwarp();
-  if (ops[0].kind == 1) {
-    for (int w = threadIdx.x; w < nr * G * 12; w += 32) {
-      const int b = w / 12, rr = NRC == 1 ? 0 : b / G;
-      if (b - rr * G < nact) sop_row(pick(ops, rr), tile + w * R, w % 12, Ls);
-    }
+  if (op.kind == 1) {
+    for (int w = threadIdx.x; w < nact * 12; w += 32) sop_row(op, tile + w * R, w % 12, Ls);
     __syncwarp();
     if (act) tile_get_pair(tile, R, bi, j, Lh, Ls, re, im);
   } else if (act) {
     // dense fallback: row s of the (already transposed where needed) matrix
-    const SOpK<float> op = pick(ops, NRC == 1 ? 0 : r);
     const float* base = tile + (bi * 12) * R;
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
@@ -360,20 +346,20 @@ __device__ __forceinline__ void sop_pair(const SOpK<float>* ops, float2* re, flo
 // ---------------------------------------------------------------- the pipelined kernel
 
 struct Ctx {        // per-CTA shared-memory layout (byte offsets)
-  int slot_bytes;   // one ring slot: G x nr site blocks (+ FP16 scales), or the s-op tile
+  int slot_bytes;   // one ring slot: G site blocks (+ FP16 scales), or the s-op tile
   int raw_off;      // two link buffers (groups alternate), one padded block per site
   int link_stride;  // bytes between two sites' link blocks
-  int nb_off;       // neighbour indices [2 groups][8 directions][G nr copy lanes]
+  int nb_off;       // neighbour indices [2 groups][8 directions][G sites]
+  int part_off;     // per-right-hand-side partial sums [kMaxBatch][32] (batched launches)
   int total;
 };
 
 // need_tile: an epilogue runs through shared memory (odd Ls or a dense operator)
-__host__ __device__ inline Ctx make_ctx(int Ls, int prec, int G, int nr, bool need_tile) {
+__host__ __device__ inline Ctx make_ctx(int Ls, int prec, int G, bool batched, bool need_tile) {
   const int Lh = (Ls + 1) / 2;
   const int cb = prec == DWF_F32 ? 16 : 8;
-  const int nb = G * nr;
-  const int blocks = nb * 12 * Lh * cb + (prec == DWF_F16 ? nb * Lh * 8 : 0);
-  const int tile = need_tile ? nb * 12 * tile_row(Ls) * 4 : 0;
+  const int blocks = G * 12 * Lh * cb + (prec == DWF_F16 ? G * Lh * 8 : 0);
+  const int tile = need_tile ? G * 12 * tile_row(Ls) * 4 : 0;
   int slot = blocks > tile ? blocks : tile;
   slot = (slot + 127) / 128 * 128;
   Ctx c;
@@ -382,7 +368,8 @@ __host__ __device__ inline Ctx make_ctx(int Ls, int prec, int G, int nr, bool ne
   // 8 links x 18 reals per site, +16 bytes so consecutive sites start in different banks
   c.link_stride = 8 * 18 * (prec == DWF_F32 ? 4 : 2) + 16;
   c.nb_off = c.raw_off + 2 * G * c.link_stride;
-  c.total = c.nb_off + 2 * 8 * nb * 4;
+  c.part_off = (c.nb_off + 2 * 8 * G * 4 + 7) / 8 * 8;
+  c.total = c.part_off + (batched ? kMaxBatch * 32 * 8 : 0);
   return c;
 }
 
@@ -408,23 +395,19 @@ template <class S> struct Pipe {
   unsigned char* sm;
   unsigned bar0;
   int blk, sblk;
-  int nr;                         // right-hand sides of the launch
-  int* nbs;                       // neighbour table in shared memory
-  const unsigned char* src_in;    // this lane's copy source: in[lane / G] (lane < G nr)
-  const unsigned char* src_in_n;  // its FP16 scales
-  const unsigned char* src_x;     // x[lane] (lane < nr)
-  const unsigned char* src_x_n;
-  const unsigned char* src_run;   // in[lane] (lane < nr): whole-group copies
-  const unsigned char* src_run_n;
+  int* nbs;  // neighbour table in shared memory
 };
 
-// Issue stage k of group g into ring slot `slot` (all lanes call).  Slot
-// block t = r * G + i holds site i of right-hand side r and is fetched by
-// lane t; the group's neighbour indices and links sit in buffer lb.
-template <class S>
-__device__ __forceinline__ void issue_stage(const Pipe<S>& P, long g, int k, int slot, int lb) {
+// Issue stage t of group g into ring slot `slot` (all lanes call).  Stage
+// t = r * NST + d of a group is, for right-hand side r, neighbour direction
+// d < 8 (the G neighbour blocks, site i into slot block i; stage 0 also brings
+// the group's links) or d = 8, the group's own blocks of the site term.  The
+// group's neighbour indices and links sit in buffer lb.
+template <class S, int NST>
+__device__ __forceinline__ void issue_stage(const Pipe<S>& P, long g, int t, int slot, int lb) {
   const Hop3Args<S>& a = *P.a;
   if (g >= a.ngroups) return;
+  const int r = t / NST, d = t - r * NST;
   const long h0 = g * a.G;
   const long left = a.Vh - h0;
   const int nact = left < a.G ? (int)left : a.G;
@@ -433,40 +416,47 @@ __device__ __forceinline__ void issue_stage(const Pipe<S>& P, long g, int k, int
   unsigned char* dst = P.sm + slot * a.ctx.slot_bytes;
   const bool fp16 = sizeof(S) == 2;
   const int lbytes = 8 * 18 * (int)sizeof(S);
-  const int nb = a.G * P.nr;
+  const int G = a.G;
   // earlier generic-proxy reads of this slot must be ordered before the copies
   fence_async_smem();
-  const unsigned bytes = nact * P.nr * (P.blk + (fp16 ? P.sblk : 0)) + (k == 0 ? nact * lbytes : 0);
+  const unsigned bytes = nact * (P.blk + (fp16 ? P.sblk : 0)) + (t == 0 ? nact * lbytes : 0);
   if (lane == 0) mbar_expect_tx(bar, bytes);
   __syncwarp();
-  if (k < 8) {
-    const int nb_k = lane < nb ? P.nbs[(lb * 8 + k) * nb + lane] : 0;
+  if (d < 8) {
+    const CFieldRef<S> src = a.in[r];
+    const int nb_k = lane < G ? P.nbs[(lb * 8 + d) * G + lane] : 0;
     // When the group's neighbours in this direction are consecutive sites (a
     // group inside one x-row, whose y/z/t neighbours shift as a block), one
-    // copy per right-hand side moves them all; otherwise one copy per site.
+    // copy moves them all; otherwise one copy per site.
     const int nb0 = __shfl_sync(0xffffffffu, nb_k, 0);
     const unsigned run = __ballot_sync(0xffffffffu, lane >= nact || nb_k == nb0 + lane);
     if (run == 0xffffffffu) {
-      if (lane < P.nr) {
-        bulk_g2s(smem_addr(dst + lane * a.G * P.blk), P.src_run + (long)nb0 * P.blk, nact * P.blk, bar);
+      if (lane == 0) {
+        bulk_g2s(smem_addr(dst), reinterpret_cast<const unsigned char*>(src.v) + (long)nb0 * P.blk, nact * P.blk,
+                 bar);
         if (fp16)
-          bulk_g2s(smem_addr(dst + nb * P.blk + lane * a.G * P.sblk), P.src_run_n + (long)nb0 * P.sblk,
+          bulk_g2s(smem_addr(dst + G * P.blk), reinterpret_cast<const unsigned char*>(src.norm) + (long)nb0 * P.sblk,
                    nact * P.sblk, bar);
       }
-    } else if (lane < nb && lane % a.G < nact) {
-      bulk_g2s(smem_addr(dst + lane * P.blk), P.src_in + (long)nb_k * P.blk, P.blk, bar);
-      if (fp16) bulk_g2s(smem_addr(dst + nb * P.blk + lane * P.sblk), P.src_in_n + (long)nb_k * P.sblk, P.sblk, bar);
+    } else if (lane < nact) {
+      bulk_g2s(smem_addr(dst + lane * P.blk), reinterpret_cast<const unsigned char*>(src.v) + (long)nb_k * P.blk,
+               P.blk, bar);
+      if (fp16)
+        bulk_g2s(smem_addr(dst + G * P.blk + lane * P.sblk),
+                 reinterpret_cast<const unsigned char*>(src.norm) + (long)nb_k * P.sblk, P.sblk, bar);
     }
-    if (k == 0 && lane < nact) {
+    if (t == 0 && lane < nact) {
       // the links of consecutive groups of this CTA alternate between two
       // buffers: this copy is issued while the previous group still reads its own
-      bulk_g2s(smem_addr(P.sm + a.ctx.raw_off + (lb * a.G + lane) * a.ctx.link_stride),
+      bulk_g2s(smem_addr(P.sm + a.ctx.raw_off + (lb * G + lane) * a.ctx.link_stride),
                a.links + (h0 + lane) * 8 * 18, lbytes, bar);
     }
-  } else if (lane < P.nr) {
-    bulk_g2s(smem_addr(dst + lane * a.G * P.blk), P.src_x + h0 * P.blk, nact * P.blk, bar);
+  } else if (lane == 0) {
+    const CFieldRef<S> src = a.x[r];
+    bulk_g2s(smem_addr(dst), reinterpret_cast<const unsigned char*>(src.v) + h0 * P.blk, nact * P.blk, bar);
     if (fp16)
-      bulk_g2s(smem_addr(dst + nb * P.blk + lane * a.G * P.sblk), P.src_x_n + h0 * P.sblk, nact * P.sblk, bar);
+      bulk_g2s(smem_addr(dst + G * P.blk), reinterpret_cast<const unsigned char*>(src.norm) + h0 * P.sblk,
+               nact * P.sblk, bar);
   }
 }
 
@@ -485,7 +475,7 @@ __device__ __forceinline__ void read_pair(const Pipe<S>& P, const unsigned char*
     }
   } else {
     const uint2* c2 = reinterpret_cast<const uint2*>(slot + bi * P.blk);
-    const float2 sc = reinterpret_cast<const float2*>(slot + P.a->G * P.nr * P.blk + bi * P.sblk)[j];
+    const float2 sc = reinterpret_cast<const float2*>(slot + P.a->G * P.blk + bi * P.sblk)[j];
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
       const uint2 v = c2[k * Lh + j];
@@ -512,61 +502,53 @@ __device__ __forceinline__ void site_links(const Pipe<S>& P, int lb, int i, int 
   }
 }
 
-// Lane (i, r, j) = lane / (nr Lh), ... owns slice pair j of site i of
-// right-hand side r; a group is G consecutive sites of all nr right-hand sides.
-template <class S, int DAG, int HX, int NRC>
+// Lane (i, j) = (lane / Lh, lane % Lh) owns slice pair j of site i of a group
+// of G consecutive sites.  A batched launch (BATCH = 1) walks the group's
+// stages for each right-hand side in turn: the links and neighbour indices
+// of a group are staged once for all of them, every other quantity is the
+// single-field kernel's.
+template <class S, int DAG, int HX, int BATCH>
 __global__ void __launch_bounds__(32, 12) hop3_kernel(const Hop3Args<S> a) {
   extern __shared__ __align__(128) unsigned char sm[];
   __shared__ __align__(8) unsigned long long bars[kSlots];
   __shared__ double red[32];
-  constexpr int NST = HX ? 9 : 8;  // stages per group
-  const int Lh = a.Lh, G = a.G, Ls = a.Ls, nr = NRC ? NRC : a.nr;
+  constexpr int NST = HX ? 9 : 8;  // stages per right-hand side and group
+  const int Lh = a.Lh, G = a.G, Ls = a.Ls;
+  const int NSG = BATCH ? a.nr * NST : NST;  // stages per group
   const int lane = threadIdx.x;
-  const int NJ = nr * Lh;
-  const int i = lane / NJ;
-  const int r = NRC == 1 ? 0 : (lane - i * NJ) / Lh;
-  const int j = lane - i * NJ - r * Lh;
-  const int bi = r * G + i;  // this lane's block in a slot or the tile
+  const int i = lane / Lh;
+  const int j = lane - i * Lh;
+  const int bi = i;  // this lane's block in a slot or the tile
+  double* sp = reinterpret_cast<double*>(sm + a.ctx.part_off);  // batched: [kMaxBatch][32]
   Pipe<S> P;
   P.a = &a;
   P.sm = sm;
   P.bar0 = smem_addr(&bars[0]);
   P.blk = 12 * Lh * chunk_bytes<S>();
   P.sblk = Lh * 8;
-  P.nr = nr;
   P.nbs = reinterpret_cast<int*>(sm + a.ctx.nb_off);
-  {
-    const int rc = (NRC == 1 || lane >= G * nr) ? 0 : lane / G;
-    const CFieldRef<S> fin = pick(a.in, rc);
-    P.src_in = reinterpret_cast<const unsigned char*>(fin.v);
-    P.src_in_n = reinterpret_cast<const unsigned char*>(fin.norm);
-    const CFieldRef<S> fx = pick(a.x, (NRC == 1 || lane >= nr) ? 0 : lane);
-    P.src_x = reinterpret_cast<const unsigned char*>(fx.v);
-    P.src_x_n = reinterpret_cast<const unsigned char*>(fx.norm);
-    const CFieldRef<S> fr = pick(a.in, (NRC == 1 || lane >= nr) ? 0 : lane);
-    P.src_run = reinterpret_cast<const unsigned char*>(fr.v);
-    P.src_run_n = reinterpret_cast<const unsigned char*>(fr.norm);
-  }
   if (lane == 0) {
     for (int s = 0; s < kSlots; ++s) mbar_init(P.bar0 + 8u * s, 1);
     fence_async_smem();
   }
+  if (BATCH)
+    for (int q = 0; q < kMaxBatch; ++q) sp[q * 32 + lane] = 0.0;
   __syncwarp();
   const long stride = gridDim.x;
-  // neighbour indices of a group for this lane's copy site, into buffer lb
+  // neighbour indices of a group for this lane's site, into buffer lb
   // (each lane reads back only what it wrote)
   auto load_nb = [&](long g, int lb) {
-    if (lane < G * nr) {
-      const long hh = g * G + lane % G;
+    if (lane < G) {
+      const long hh = g * G + lane;
       const bool ok = g < a.ngroups && hh < a.Vh;
 #pragma unroll
-      for (int d = 0; d < 8; ++d) P.nbs[(lb * 8 + d) * G * nr + lane] = ok ? __ldg(a.nbr + (long)d * a.Vh + hh) : 0;
+      for (int d = 0; d < 8; ++d) P.nbs[(lb * 8 + d) * G + lane] = ok ? __ldg(a.nbr + (long)d * a.Vh + hh) : 0;
     }
   };
   long g = blockIdx.x;
   load_nb(g, 0);
 #pragma unroll
-  for (int s = 0; s < kSlots; ++s) issue_stage<S>(P, g, s, s, 0);
+  for (int s = 0; s < kSlots; ++s) issue_stage<S, NST>(P, g, s, s, 0);
   unsigned seq = 0;  // global index of the stage being consumed; slot seq % kSlots
   bool bad = false;
   double part = 0.0;
@@ -584,81 +566,95 @@ __global__ void __launch_bounds__(32, 12) hop3_kernel(const Hop3Args<S> a) {
       ai[k] = ar[k];
     }
 #pragma unroll 1
-    for (int d = 0; d < 8; ++d) {
+    for (int t = 0; t < NSG; ++t) {
+      const int r = BATCH ? t / NST : 0;
+      const int d = t - r * NST;
       const int slot = seq % kSlots;
+      unsigned char* sl = sm + slot * a.ctx.slot_bytes;
       if (!mbar_wait(P.bar0 + 8u * slot, (seq / kSlots) & 1)) bad = true;
-      if (act) {
-        float2 pr[12], pi[12], U[9];
-        read_pair<S>(P, sm + slot * a.ctx.slot_bytes, bi, j, pr, pi);
-        site_links<S>(P, lb, i, d, U);
-        // (1 - sg g_mu): sg = +1 forward / -1 backward, flipped by the dagger
-        const float sg = ((d < 4) != (DAG != 0)) ? 1.f : -1.f;
-        switch (d & 3) {
-          case 0: hop_dir2<0>(sg, pr, pi, U, ar, ai); break;
-          case 1: hop_dir2<1>(sg, pr, pi, U, ar, ai); break;
-          case 2: hop_dir2<2>(sg, pr, pi, U, ar, ai); break;
-          default: hop_dir2<3>(sg, pr, pi, U, ar, ai); break;
+      float2 xr[12], xi[12];  // the site term (d = 8)
+      if (d < 8) {
+        if (act) {
+          float2 pr[12], pi[12], U[9];
+          read_pair<S>(P, sl, bi, j, pr, pi);
+          site_links<S>(P, lb, i, d, U);
+          // (1 - sg g_mu): sg = +1 forward / -1 backward, flipped by the dagger
+          const float sg = ((d < 4) != (DAG != 0)) ? 1.f : -1.f;
+          switch (d & 3) {
+            case 0: hop_dir2<0>(sg, pr, pi, U, ar, ai); break;
+            case 1: hop_dir2<1>(sg, pr, pi, U, ar, ai); break;
+            case 2: hop_dir2<2>(sg, pr, pi, U, ar, ai); break;
+            default: hop_dir2<3>(sg, pr, pi, U, ar, ai); break;
+          }
+        }
+      } else if (HX) {
+        if (act) read_pair<S>(P, sl, bi, j, xr, xi);
+      }
+      __syncwarp();
+      // refill this slot with the stage kSlots ahead; after the last stage of
+      // a right-hand side the slot first serves as the epilogue's tile
+      const bool last = d == NST - 1;
+      const int k2 = t + kSlots;
+      if (!last) {
+        if (k2 < NSG)
+          issue_stage<S, NST>(P, g, k2, slot, lb);
+        else
+          issue_stage<S, NST>(P, g + stride, k2 - NSG, slot, lb ^ 1);
+      }
+      ++seq;
+      if (last) {
+        // epilogue for right-hand side r
+        const float2 sc = f2(a.scale);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+          ar[k] = __fmul2_rn(sc, ar[k]);
+          ai[k] = __fmul2_rn(sc, ai[k]);
+        }
+        float* tile = reinterpret_cast<float*>(sl);
+        if (HX) {
+          const SOpK<float> ex = a.ex[r];
+          if (ex.kind != 0) sop_pair(ex, xr, xi, tile, bi, j, act, G, nact, Ls, Lh);
+          const float2 xs = f2(a.xscale);
+#pragma unroll
+          for (int k = 0; k < 12; ++k) {
+            ar[k] = fma2(xs, xr[k], ar[k]);
+            ai[k] = fma2(xs, xi[k], ai[k]);
+          }
+        }
+        const SOpK<float> eout = a.eout[r];
+        if (eout.kind != 0) sop_pair(eout, ar, ai, tile, bi, j, act, G, nact, Ls, Lh);
+        // the delayed refill of the tile's slot
+        if (k2 < NSG)
+          issue_stage<S, NST>(P, g, k2, slot, lb);
+        else
+          issue_stage<S, NST>(P, g + stride, k2 - NSG, slot, lb ^ 1);
+        if (2 * j + 1 >= Ls) {  // odd Ls: the padding slot stays zero
+#pragma unroll
+          for (int k = 0; k < 12; ++k) {
+            ar[k].y = 0.f;
+            ai[k].y = 0.f;
+          }
+        }
+        if (act && !bad) {
+          store_pair(a.out[r], h0 + i, j, Lh, ar, ai);
+          float2 p0 = make_float2(0.f, 0.f), p1 = p0;
+#pragma unroll
+          for (int k = 0; k < 12; ++k) {
+            p0 = fma2(ar[k], ar[k], p0);
+            p1 = fma2(ai[k], ai[k], p1);
+          }
+          const double ps = (double)((p0.x + p0.y) + (p1.x + p1.y));
+          if (BATCH)
+            sp[r * 32 + lane] += ps;
+          else
+            part += ps;
+        }
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+          ar[k] = make_float2(0.f, 0.f);
+          ai[k] = ar[k];
         }
       }
-      __syncwarp();
-      // refill this slot with the stage kSlots ahead; after the group's last
-      // stage the slot first serves as the epilogue's tile
-      if (d != NST - 1) {
-        const int k2 = d + kSlots;
-        if (k2 < NST)
-          issue_stage<S>(P, g, k2, slot, lb);
-        else
-          issue_stage<S>(P, g + stride, k2 - NST, slot, lb ^ 1);
-      }
-      ++seq;
-    }
-    // epilogue
-    const float sc = a.scale;
-#pragma unroll
-    for (int k = 0; k < 12; ++k) {
-      ar[k] = make_float2(ar[k].x * sc, ar[k].y * sc);
-      ai[k] = make_float2(ai[k].x * sc, ai[k].y * sc);
-    }
-    int tslot;
-    if (HX) {
-      tslot = seq % kSlots;
-      if (!mbar_wait(P.bar0 + 8u * tslot, (seq / kSlots) & 1)) bad = true;
-      float2 xr[12], xi[12];
-      if (act) read_pair<S>(P, sm + tslot * a.ctx.slot_bytes, bi, j, xr, xi);
-      __syncwarp();
-      float* tile = reinterpret_cast<float*>(sm + tslot * a.ctx.slot_bytes);
-      if (a.ex[0].kind != 0) sop_pair<NRC>(a.ex, xr, xi, tile, bi, r, j, act, G, nact, nr, Ls, Lh);
-      const float2 xs = f2(a.xscale);
-#pragma unroll
-      for (int k = 0; k < 12; ++k) {
-        ar[k] = fma2(xs, xr[k], ar[k]);
-        ai[k] = fma2(xs, xi[k], ai[k]);
-      }
-      ++seq;
-    } else {
-      tslot = (seq - 1) % kSlots;
-    }
-    if (a.eout[0].kind != 0)
-      sop_pair<NRC>(a.eout, ar, ai, reinterpret_cast<float*>(sm + tslot * a.ctx.slot_bytes), bi, r, j, act, G, nact, nr,
-               Ls, Lh);
-    // the delayed refill of the tile's slot: the next group's stage kSlots - 1
-    issue_stage<S>(P, g + stride, kSlots - 1, tslot, lb ^ 1);
-    if (2 * j + 1 >= Ls) {  // odd Ls: the padding slot stays zero
-#pragma unroll
-      for (int k = 0; k < 12; ++k) {
-        ar[k].y = 0.f;
-        ai[k].y = 0.f;
-      }
-    }
-    if (act && !bad) {
-      store_pair(pick(a.out, NRC == 1 ? 0 : r), h0 + i, j, Lh, ar, ai);
-      float2 p0 = make_float2(0.f, 0.f), p1 = p0;
-#pragma unroll
-      for (int k = 0; k < 12; ++k) {
-        p0 = fma2(ar[k], ar[k], p0);
-        p1 = fma2(ai[k], ai[k], p1);
-      }
-      part += (double)((p0.x + p0.y) + (p1.x + p1.y));
     }
   }
   if (bad) {
@@ -666,28 +662,29 @@ __global__ void __launch_bounds__(32, 12) hop3_kernel(const Hop3Args<S> a) {
     for (int s = 0; s < kSlots; ++s) mbar_wait(P.bar0 + 8u * s, ((seq + s) / kSlots) & 1);  // bounded
   }
   if (a.partials[0]) {
-    // per right-hand side: sum the lanes (i, r, j) over i and j in a fixed order
-    red[lane] = part;
+    // per right-hand side: sum the lanes (i, j) in a fixed order
+    if (!BATCH) sp = red;
+    if (!BATCH) red[lane] = part;
     __syncwarp();
+    const int nr = BATCH ? a.nr : 1;
     if (lane < nr) {
       double t = 0.0;
-      for (int ii = 0; ii < G; ++ii)
-        for (int jj = 0; jj < Lh; ++jj) t += red[ii * NJ + lane * Lh + jj];
-      pick(a.partials, NRC == 1 ? 0 : lane)[blockIdx.x] = t;
+      for (int q = 0; q < G * Lh; ++q) t += sp[lane * 32 + q];
+      a.partials[lane][blockIdx.x] = t;
     }
   }
 }
 
 }  // namespace
 
-// Sites per group for the pipelined kernel over nr right-hand sides, or 0 if
-// the shape needs the per-slice kernel.
+// Sites per group for the pipelined kernel, or 0 if the shape needs the
+// per-slice kernel (a batched launch takes the same groups).
 int hop2_sites(int Ls, int prec, int nr) {
   const int Lh = (Ls + 1) / 2;
   if (prec != DWF_F32 && prec != DWF_F16) return 0;
-  if (nr < 1 || nr > kMaxBatch || nr * Lh > 32) return 0;
+  if (nr < 1 || nr > kMaxBatch || Lh > 32) return 0;
   if (prec == DWF_F16 && (Lh % 2)) return 0;  // FP16 scale blocks must be multiples of 16 bytes
-  return 32 / (nr * Lh);
+  return 32 / Lh;
 }
 
 // Resident CTAs per SM for a kernel and dynamic smem size (cached).
@@ -716,6 +713,9 @@ static int resident_per_sm(const void* kern, size_t smem, int* per_sm, int* sms_
 template <class S>
 static dwf_status hop3_t(dwf_lattice* L, const HopCall& c, const HopBatch& b, const SOpK<float>* ex,
                          const SOpK<float>* eout, int G, int ctas_per_sm) {
+  const bool dense = (c.has_x && ex[0].kind == 2) || eout[0].kind == 2;
+  const bool any = (c.has_x && ex[0].kind != 0) || eout[0].kind != 0;
+  const bool need_tile = any && ((L->Ls & 1) || dense);
   Hop3Args<S> a{};
   for (int r = 0; r < b.nrhs; ++r) {
     a.in[r] = CFieldRef<S>{reinterpret_cast<const S*>(b.in[r].v), b.in[r].norm};
@@ -725,6 +725,7 @@ static dwf_status hop3_t(dwf_lattice* L, const HopCall& c, const HopBatch& b, co
     a.eout[r] = eout[r];
     a.partials[r] = b.partials[r];
   }
+  const bool batched = b.nrhs > 1;
   a.links = reinterpret_cast<const S*>(L->links[b.in[0].prec][c.out_parity]);
   a.nbr = L->nbr[c.out_parity];
   a.Vh = L->Vh;
@@ -733,9 +734,7 @@ static dwf_status hop3_t(dwf_lattice* L, const HopCall& c, const HopBatch& b, co
   a.ngroups = (L->Vh + G - 1) / G;
   a.Ls = L->Ls;
   a.Lh = L->Lh;
-  const bool dense = (c.has_x && ex[0].kind == 2) || eout[0].kind == 2;
-  const bool any = (c.has_x && ex[0].kind != 0) || eout[0].kind != 0;
-  a.ctx = make_ctx(L->Ls, b.in[0].prec, G, b.nrhs, any && ((L->Ls & 1) || dense));
+  a.ctx = make_ctx(L->Ls, b.in[0].prec, G, batched, need_tile);
   a.scale = (float)c.scale;
   a.xscale = (float)c.xscale;
   a.err = L->dev_err;
@@ -753,7 +752,7 @@ static dwf_status hop3_t(dwf_lattice* L, const HopCall& c, const HopBatch& b, co
     if (c.nblocks) *c.nblocks = (int)grid;
     return DWF_OK;
   };
-  if (b.nrhs == 1) {
+  if (batched) {
     if (c.dag) return c.has_x ? run(hop3_kernel<S, 1, 1, 1>) : run(hop3_kernel<S, 1, 0, 1>);
     return c.has_x ? run(hop3_kernel<S, 0, 1, 1>) : run(hop3_kernel<S, 0, 0, 1>);
   }

@@ -41,7 +41,7 @@ DELTA = 0.01
 # DRAM traffic per algorithmic byte of the FP32 hop kernel, from one ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum of two launches on the
 # 24^3x48x16 Ls=16 case); it applies only to the kernel source it was taken on.
-HOP_TRAFFIC = {"source_sha256_prefix": "9964957fc816151f", "ratio": 1.088}
+HOP_TRAFFIC = {"source_sha256_prefix": "dc5de73caaafee4b", "ratio": 1.105}
 
 WORKLOADS = {
     # MADWF: Shamir 24^3 x 64 x Ls=32, m_f = 0.002, eps = 0.6, through Moebius Ls' = 12 with

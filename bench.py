@@ -213,7 +213,9 @@ def config_of(w, inner):
 def oracle_iteration_seconds(w):
     """Seconds per FP64 oracle CG iteration (M_pc then M_pc^+) on the workload,
     measured on a t-slab of sample_T timeslices and scaled to the full volume
-    (the oracle's work per site does not depend on the lattice extent)."""
+    (the oracle's work per site does not depend on the lattice extent), and the
+    host cores it kept busy: process CPU time over wall time of the timed part,
+    rounded (numpy may run its array operations on several threads)."""
     import numpy as np
 
     from oracle import dwf_oracle as O
@@ -225,11 +227,12 @@ def oracle_iteration_seconds(w):
     b = inputs.gaussian_spinor(w["seed"], dims, w["Ls"])
     eo = O.EO(U, w["m"], w["M5"], w["Ls"], w.get("b5", 1.0), w.get("c5", 0.0))
     v = b * eo.even
-    t0 = time.perf_counter()
+    t0, c0 = time.perf_counter(), time.process_time()
     q = eo.Mpc(v)
     v = eo.Mpc(q, True)
     v = v / np.sqrt(O.norm2(v))
-    return (time.perf_counter() - t0) * (T / w["sample_T"])
+    wall, cpu = time.perf_counter() - t0, time.process_time() - c0
+    return wall * (T / w["sample_T"]), max(1, round(cpu / wall))
 
 
 def sample_text(w, iters, per_it):
@@ -239,7 +242,7 @@ def sample_text(w, iters, per_it):
     what = "the summed iterations of the FP64 CG solves of the ladder's masses" if w.get("ladder") \
         else "the iterations of the FP64 CG solve of this input"
     return (f"one FP64 oracle CG iteration (M_pc then M_pc^+) on {slab} ({per_it:.1f} s per full-volume "
-            f"iteration), times {iters}, {what}")
+            f"iteration), times {iters}, {what}; numpy on a host with {os.cpu_count()} CPUs")
 
 
 def run_reference(args, w):
@@ -247,15 +250,16 @@ def run_reference(args, w):
         return
     for _ in range(args.warmup):
         oracle_iteration_seconds(w)
-    times = [oracle_iteration_seconds(w) for _ in range(args.steps)]
-    per_it = statistics.mean(times)
+    runs = [oracle_iteration_seconds(w) for _ in range(args.steps)]
+    per_it = statistics.mean(t for t, _ in runs)
+    cores = max(c for _, c in runs)
     iters = FP64_ITERS[args.workload]
     value = per_it * iters
     line = {"impl": "reference", "metric": metric_name(w), "value": value, "unit": "s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_it * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_of(w, "f64"),
-            "cpu_baseline": {"value": value, "unit": "s", "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": "s", "cores": cores, "kind": "oracle",
                              "sample": sample_text(w, iters, per_it)},
             "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -386,8 +390,8 @@ def run_ladder(args, w, inner, world, rank, local, dev, hbm_peak, peak_src):
     if rank == 0:
         if not args.no_cpu_baseline:
             iters = sum(s["iters"] for s in st)
-            per_it = oracle_iteration_seconds(w)
-            line["cpu_baseline"] = {"value": per_it * iters, "unit": "s", "cores": 1, "kind": "oracle",
+            per_it, cores = oracle_iteration_seconds(w)
+            line["cpu_baseline"] = {"value": per_it * iters, "unit": "s", "cores": cores, "kind": "oracle",
                                     "sample": sample_text(w, iters, per_it)
                                     + " (the mixed solves' iteration counts stand in for FP64 CG's)"}
         print(json.dumps(line), flush=True)
@@ -538,8 +542,8 @@ def main():
     if rank == 0:
         if not args.no_cpu_baseline:
             iters = comp["fp64_cg"]["iters"] if "fp64_cg" in comp else FP64_ITERS[args.workload]
-            per_it = oracle_iteration_seconds(w)
-            line["cpu_baseline"] = {"value": per_it * iters, "unit": "s", "cores": 1, "kind": "oracle",
+            per_it, cores = oracle_iteration_seconds(w)
+            line["cpu_baseline"] = {"value": per_it * iters, "unit": "s", "cores": cores, "kind": "oracle",
                                     "sample": sample_text(w, iters, per_it)}
         print(json.dumps(line), flush=True)
     for L in lats:

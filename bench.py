@@ -22,6 +22,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -201,6 +202,9 @@ def config_of(w, inner):
     if w["madwf"]:
         c.update({"Ls_inner": w["inner_Ls"], "b_inner": w["b"], "c_inner": w["c"], "n_dc": w["n_dc"],
                   "tol_pv": w["tol_pv"], "tol_mob": w["tol_mob"]})
+        if inner == "f32":  # the library's trigger for the FP32 intermediate solves (include/dwf.h)
+            c.update({"reliable_update_delta_pv": min(DELTA, max(math.sqrt(w["tol_pv"]), 1e-3)),
+                      "reliable_update_delta_mob": min(DELTA, max(math.sqrt(w["tol_mob"]), 1e-3))})
     if w.get("ladder"):
         c.update({"m_f": list(w["masses"]), "b": w["b5"], "c": w["c5"], "nrhs": len(w["masses"]),
                   "sources": f"Gaussian, seeds {w['seed']}..{w['seed'] + len(w['masses']) - 1}"})

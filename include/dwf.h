@@ -171,7 +171,8 @@ typedef struct {
   double tol_final;    /* target |b - D(m) x| / |b| of the final DWF solve */
   dwf_prec inner;      /* precision of the inner CG iterations */
   int max_iter;        /* iteration cap per solve */
-  double delta;        /* reliable-update trigger of every solve */
+  double delta;        /* reliable-update trigger of every solve; with DWF_F32 the Pauli-Villars
+                          and Moebius solves use min(delta, max(sqrt(their tolerance), 1e-3)) */
   int check_every;     /* host convergence polls */
 } madwf_params;
 

@@ -14,6 +14,7 @@
 //
 // P shifts the P+ half of the spinor by one slice: (P y)_s = P- y_s + P+ y_{s+1},
 // (P^-1 x)_s = P- x_s + P+ x_{s-1} (indices mod Ls); the paper's slice "1" is s = 0.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 
@@ -180,8 +181,17 @@ extern "C" dwf_status madwf_solve(dwf_lattice_t L, dwf_lattice_t Li, double m, c
   DWF_TRY(norm_pair(L, be, bo, &bnorm));
   if (!std::isfinite(bnorm)) return fail(L, DWF_ERR_NAN, "madwf_solve: non-finite source");
 
-  dwf_cg_params pv{prm->tol_pv, prm->max_iter, prm->inner, prm->delta, prm->check_every};
-  dwf_cg_params mob{prm->tol_mob, prm->max_iter, prm->inner, prm->delta, prm->check_every};
+  // The intermediate solves only need their own loose tolerance.  With FP32
+  // inner iterations an FP64 reliable update once the residual has dropped
+  // by sqrt(tol) (but by no more than 1e-3: over such a reduction the FP32
+  // rounding of the recursed residual stays far below the residual) keeps the
+  // recursion accurate enough and saves an FP64 residual per solve against a
+  // trigger of 1e-2; FP16 storage keeps the caller's delta.
+  auto inter_delta = [&](double tol) {
+    return prm->inner == DWF_F32 ? std::min(prm->delta, std::max(std::sqrt(tol), 1e-3)) : prm->delta;
+  };
+  dwf_cg_params pv{prm->tol_pv, prm->max_iter, prm->inner, inter_delta(prm->tol_pv), prm->check_every};
+  dwf_cg_params mob{prm->tol_mob, prm->max_iter, prm->inner, inter_delta(prm->tol_mob), prm->check_every};
   dwf_cg_params fin{prm->tol_final, prm->max_iter, prm->inner, prm->delta, prm->check_every};
 
   dwf_status status = DWF_OK;

@@ -13,7 +13,9 @@ step is a plain linear-algebra definition.
 
 Paper: Yin & Mawhinney, "Improving DWF Simulations: the Force Gradient
 Integrator and the Moebius Accelerated DWF Solver" (Lattice 2011).
-  Sec. 2 (Eqs. 1-6)   force-gradient PQPQP integrator, U' = exp(-tau^2/24 F^j T_j) U
+  Sec. 2 (Eqs. 1-6)   force-gradient PQPQP integrator, U' = exp(-tau^2/24 F^j T_j) U;
+                      the Omelyan 2MN integrator it is compared with, whole
+                      trajectories and the Metropolis test
   Sec. 3 (Eqs. 7-8)   Hasenbusch quotient actions
   Sec. 4 (Eqs. 9-16)  D_DW(m) x = b, the domain-wall -> overlap transformation,
                       Eq. (ov_eq), (trans_5d_4d_source), (dwf_eq_4d), (mob_eq_4d),
@@ -613,3 +615,68 @@ def hamiltonian(U, p, phis, terms, M5, b=1.0, c=0.0, bc_t=1, tol=1e-13):
     S = sum(quotient_solution(U, phi, m1, m2, M5, b, c, bc_t, tol)[2]
             for (m1, m2), phi in zip(terms, phis))
     return 0.5 * float(np.sum(p * p)) + S
+
+
+# ---------------------------------------------------------------------------
+# Trajectories: the force-gradient integrator against Omelyan's (Sec. 2)
+# ---------------------------------------------------------------------------
+
+# The second-order minimum-norm ("2MN") parameter of Omelyan, Mryglod and
+# Folk, Comput. Phys. Commun. 151 (2003) 272 -- the integrator Sec. 2
+# compares the force-gradient integrator with.
+OMELYAN_LAMBDA = 0.1931833275037836
+
+
+def omelyan_step(U, p, tau, phis, terms, M5, b=1.0, c=0.0, bc_t=1, tol=1e-13, lam=OMELYAN_LAMBDA):
+    """One Omelyan 2MN step: P(lam tau) Q(tau/2) P((1 - 2 lam) tau) Q(tau/2) P(lam tau)."""
+    _, F, _ = action_and_force(U, phis, terms, M5, b, c, bc_t, tol)
+    p = p - lam * tau * F
+    U = link_update(U, p, tau / 2)
+    _, F, _ = action_and_force(U, phis, terms, M5, b, c, bc_t, tol)
+    p = p - (1.0 - 2.0 * lam) * tau * F
+    U = link_update(U, p, tau / 2)
+    _, F, _ = action_and_force(U, phis, terms, M5, b, c, bc_t, tol)
+    p = p - lam * tau * F
+    return U, p
+
+
+def md_trajectory(U, p, tau, nsteps, phis, terms, M5, b=1.0, c=0.0, bc_t=1, tol=1e-13, integrator="fgi"):
+    """nsteps steps of length tau of the force-gradient integrator (as in
+    fgi_step, with forecasting) or of Omelyan's 2MN (omelyan_step).
+
+    The closing momentum update of a step and the opening one of the next use
+    the force at the same U, so they are applied as one update of twice the
+    weight: a trajectory evaluates the force 3 nsteps + 1 (FGI) or
+    2 nsteps + 1 (Omelyan) times instead of 4 nsteps or 3 nsteps.
+    Returns (U, p, force evaluations)."""
+    if integrator not in ("fgi", "omelyan"):
+        raise ValueError(integrator)
+    a = 1.0 / 6.0 if integrator == "fgi" else OMELYAN_LAMBDA  # weight of the end momentum updates
+    count = 0
+
+    def force(Ux, guesses=None):
+        nonlocal count
+        count += 1
+        return action_and_force(Ux, phis, terms, M5, b, c, bc_t, tol, guesses=guesses)
+
+    _, F, _ = force(U)
+    p = p - a * tau * F
+    for k in range(nsteps):
+        U = link_update(U, p, tau / 2)
+        if integrator == "fgi":
+            _, F, sols = force(U)
+            _, Fp, _ = force(link_update(U, F, -tau * tau / 24), guesses=sols)
+            p = p - 2.0 / 3.0 * tau * Fp
+        else:
+            _, F, _ = force(U)
+            p = p - (1.0 - 2.0 * a) * tau * F
+        U = link_update(U, p, tau / 2)
+        _, F, _ = force(U)
+        p = p - (a if k == nsteps - 1 else 2.0 * a) * tau * F
+    return U, p, count
+
+
+def metropolis_accept(dH: float, u: float) -> bool:
+    """Accept a trajectory with probability min(1, exp(-dH)); u is a uniform
+    number in [0, 1) that the caller draws."""
+    return dH <= 0.0 or u < float(np.exp(-dH))

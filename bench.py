@@ -34,6 +34,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 HBM_FALLBACK_GBS = 6800.0
+HBM_NOMINAL_GBS = 7900.0  # GB300 HBM3e data-sheet bandwidth, reported beside the measured peak
 
 # reliable-update threshold of the mixed-precision solves: the FP64 residual is
 # recomputed when the iterated one has dropped by this factor
@@ -369,6 +370,7 @@ def run_ladder(args, w, inner, world, rank, local, dev, hbm_peak, peak_src):
     achieved = kt["bytes"] / (kt["ms"] / 1e3) / 1e9 if kt["ms"] > 0 else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
             "frac": (achieved / hbm_peak) if achieved else None,
+            "frac_of_nominal_7900_gbs": (achieved / HBM_NOMINAL_GBS) if achieved else None,
             "traffic": hop_traffic(kt["bytes"] / max(1, kt["launches"])) if inner == "f32" else None,
             "kernel": f"hop3_kernel<{inner}> batched over right-hand sides (Wilson hop at every s, fused "
                       "fifth-dimension epilogues per mass)",
@@ -517,6 +519,7 @@ def main():
     achieved = kt["bytes"] / (kt["ms"] / 1e3) / 1e9 if kt["ms"] > 0 else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
             "frac": (achieved / hbm_peak) if achieved else None,
+            "frac_of_nominal_7900_gbs": (achieved / HBM_NOMINAL_GBS) if achieved else None,
             "traffic": hop_traffic(kt["bytes"] / max(1, kt["launches"])) if inner == "f32" else None,
             "traffic_source": "ncu DRAM read+write per algorithmic byte on 24^3x48x16 Ls=16, scaled to this launch size",
             "kernel": f"hop3_kernel<{inner}> (Wilson hop at every s with fused fifth-dimension epilogues)",

@@ -40,7 +40,9 @@ void load_file_locked() {
     std::istringstream is(line);
     std::string key;
     HopChoice c;
-    if (is >> key >> c.batch >> c.ctas_per_sm >> c.ms && c.batch >= 1) g_cache[key] = c;
+    // entries a launch could not take are skipped (the shape is then tuned again)
+    if (is >> key >> c.batch >> c.ctas_per_sm >> c.ms && c.batch >= 1 && c.batch <= kMaxBatch && c.ctas_per_sm >= 0)
+      g_cache[key] = c;
   }
   std::fclose(f);
 }

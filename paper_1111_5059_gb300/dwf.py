@@ -219,24 +219,31 @@ class Lattice:
         return n.value
 
     def set_gauge(self, U: torch.Tensor):
+        """Pack the links (complex128 [4][T][Z][Y][X][3][3] on this lattice's
+        GPU) into the library's FP64/FP32/FP16 copies."""
         self._call(lib().dwf_set_gauge, _VP(_ptr(U, self.gauge_shape)))
 
     def _new(self):
         return torch.empty(self.spinor_shape, dtype=torch.complex128, device=self.device)
 
     def apply_M(self, m: float, x: torch.Tensor, dag: bool = False, out=None) -> torch.Tensor:
+        """D(m) x (or D(m)^+ x) on the whole 5D lattice: D_DW of Sec. 4, Eq. dirac_eq
+        (Moebius with this lattice's b, c)."""
         out = self._new() if out is None else out
         fn = lib().dwf_apply_Mdag if dag else lib().dwf_apply_M
         self._call(fn, float(m), _VP(_ptr(x, self.spinor_shape)), _VP(_ptr(out, self.spinor_shape)))
         return out
 
     def apply_MdagM(self, m: float, x: torch.Tensor, out=None) -> torch.Tensor:
+        """D(m)^+ D(m) x on the whole 5D lattice."""
         out = self._new() if out is None else out
         self._call(lib().dwf_apply_MdagM, float(m), _VP(_ptr(x, self.spinor_shape)),
                    _VP(_ptr(out, self.spinor_shape)))
         return out
 
     def apply_Mpc(self, m: float, x: torch.Tensor, dag: bool = False, out=None) -> torch.Tensor:
+        """The even-odd Schur operator M_pc = A - M_eo A^-1 M_oe (or its adjoint) on
+        the even sites of x; odd sites of the result are zero."""
         out = self._new() if out is None else out
         self._call(lib().dwf_apply_Mpc, float(m), int(bool(dag)), _VP(_ptr(x, self.spinor_shape)),
                    _VP(_ptr(out, self.spinor_shape)))
@@ -252,6 +259,10 @@ class Lattice:
 
     def cg(self, m: float, b: torch.Tensor, x0=None, tol=1e-10, max_iter=100000, inner="f64",
            delta=0.1, check_every=10, raise_on_fail=True) -> SolveResult:
+        """Solve D(m) x = b (Sec. 4, Eq. dirac_eq) by even-odd CG on the normal
+        equations to |b - D(m) x| / |b| <= tol: plain FP64 (inner="f64") or mixed
+        precision with FP32 / FP16-stored inner iterations and FP64 reliable
+        updates (delta).  x0 is the initial guess (zeros if None)."""
         x = torch.zeros_like(b) if x0 is None else x0.clone()
         prm = CGParams(float(tol), int(max_iter), _PREC[inner], float(delta), int(check_every))
         st = Stats()
@@ -349,11 +360,13 @@ def fgi_link_update(lat: Lattice, X: torch.Tensor, coeff: float, U_in: torch.Ten
 
 
 def momentum_update(lat: Lattice, F: torch.Tensor, coeff: float, p: torch.Tensor):
+    """p += coeff * F on su(3) components (the P step of Sec. 2), in place."""
     lat._call(lib().dwf_momentum_update, _VP(_ptr(F, dtype=torch.float64)), float(coeff),
               _VP(_ptr(p, dtype=torch.float64)))
 
 
 def kinetic(lat: Lattice, p: torch.Tensor) -> float:
+    """1/2 sum (p^j)^2 in FP64 (the kinetic part of H, Sec. 2)."""
     T = ctypes.c_double()
     lat._call(lib().dwf_kinetic, _VP(_ptr(p, dtype=torch.float64)), ctypes.byref(T))
     return T.value

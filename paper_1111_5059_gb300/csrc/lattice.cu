@@ -5,6 +5,7 @@
 #include <mutex>
 
 #include "dwf_internal.h"
+#include "geometry.h"
 
 static std::mutex g_err_mu;
 static std::string g_err;  // last error of calls without a valid handle
@@ -544,26 +545,8 @@ dwf_status dwf_create_lattice(const dwf_params* p, void* stream, dwf_lattice_t* 
   L->stream = reinterpret_cast<cudaStream_t>(stream);
   // neighbour tables
   std::vector<int> nb((size_t)8 * L->Vh);
-  const int ext[4] = {L->X, L->Y, L->Z, L->T};
   for (int par = 0; par < 2; ++par) {
-    for (long h = 0; h < L->Vh; ++h) {
-      const int Xh = L->X / 2;
-      long rest = h / Xh;
-      const int xh = (int)(h % Xh);
-      const int y = (int)(rest % L->Y);
-      rest /= L->Y;
-      const int z = (int)(rest % L->Z);
-      const int t = (int)(rest / L->Z);
-      const int x = 2 * xh + ((par + y + z + t) & 1);
-      const int c[4] = {x, y, z, t};
-      for (int d = 0; d < 8; ++d) {
-        int q[4] = {c[0], c[1], c[2], c[3]};
-        const int mu = d & 3;
-        q[mu] = (q[mu] + (d < 4 ? 1 : ext[mu] - 1)) % ext[mu];
-        const long n = (((long)q[3] * L->Z + q[2]) * L->Y + q[1]) * L->X + q[0];
-        nb[(size_t)d * L->Vh + h] = (int)(n >> 1);
-      }
-    }
+    build_neighbour_table(L->X, L->Y, L->Z, L->T, par, nb.data());
     cudaError_t e = cudaMalloc(&L->nbr[par], nb.size() * sizeof(int));
     if (e == cudaSuccess) e = cudaMemcpy(L->nbr[par], nb.data(), nb.size() * sizeof(int), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {

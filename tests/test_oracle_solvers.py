@@ -178,6 +178,24 @@ def test_force_matches_finite_differences(masses):
     assert np.abs(np.trace(Fm, axis1=-2, axis2=-1)).max() < 1e-13
 
 
+def test_quotient_force_vanishes_for_equal_masses_and_grows_linearly():
+    """Sec. 3: the quotient det(M(m1)^+ M(m1)) / det(M(m2)^+ M(m2)) is 1 for
+    m1 = m2, so S = |phi|^2 whatever the links and the force is zero; for a
+    split m2 = m1 + mu the force is proportional to mu at small mu."""
+    dims, Ls, m = (4, 2, 2, 4), 4, 0.1
+    U = I.gauge_field(18, dims, 0.5)
+    eo = O.EO(U, m, M5, Ls)
+    phi = _src(19, dims, Ls) * eo.even
+    X, Y, S, _ = O.quotient_solution(U, phi, m, m, M5, tol=1e-14)
+    assert abs(S - O.norm2(phi)) < 1e-11 * O.norm2(phi)
+    assert np.abs(O.quotient_force(U, X, Y, phi, m, m, M5)).max() < 1e-10
+    norms = []
+    for mu in (1e-3, 2e-3):
+        X, Y, _, _ = O.quotient_solution(U, phi, m, m + mu, M5, tol=1e-14)
+        norms.append(np.abs(O.quotient_force(U, X, Y, phi, m, m + mu, M5)).max())
+    assert 1.9 < norms[1] / norms[0] < 2.1, norms
+
+
 def test_su3_exp_matches_expm():
     rng = np.random.default_rng(3)
     comp = rng.standard_normal((5, 8)) * 2

@@ -240,6 +240,18 @@ def oracle_iteration_seconds(w):
     return wall * (T / w["sample_T"]), max(1, round(cpu / wall))
 
 
+def oracle_rates(w, per_it):
+    """The oracle's rates from its time per full-volume CG iteration, which
+    applies the Wilson hop four times (M_pc and M_pc^+, two hops each): hops
+    per second over the whole 5D half lattice, and algorithmic FP64 GB/s (each
+    spinor read or written once and the 8 links once per 4D site:
+    48*8 + 144*8/Ls bytes per 5D half site and hop)."""
+    X, Y, Z, T = w["dims"]
+    sites = X * Y * Z * T // 2 * w["Ls"]
+    bytes_per_hop = (48 * 8 + 144 * 8 / w["Ls"]) * sites
+    return {"hops_per_s": 4.0 / per_it, "algorithmic_gbs": 4.0 * bytes_per_hop / per_it / 1e9}
+
+
 def sample_text(w, iters, per_it):
     X, Y, Z, T = w["dims"]
     slab = f"a {X}x{Y}x{Z}x{w['sample_T']} t-slab scaled by {T // w['sample_T']}" if w["sample_T"] < T \
@@ -264,8 +276,8 @@ def run_reference(args, w):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_it * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_of(w, "f64"),
-            "cpu_baseline": {"value": value, "unit": "s", "cores": cores, "kind": "oracle",
-                             "sample": sample_text(w, iters, per_it)},
+            "cpu_baseline": dict({"value": value, "unit": "s", "cores": cores, "kind": "oracle",
+                                  "sample": sample_text(w, iters, per_it)}, **oracle_rates(w, per_it)),
             "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -400,6 +412,7 @@ def run_ladder(args, w, inner, world, rank, local, dev, hbm_peak, peak_src):
             line["cpu_baseline"] = {"value": per_it * iters, "unit": "s", "cores": cores, "kind": "oracle",
                                     "sample": sample_text(w, iters, per_it)
                                     + " (the mixed solves' iteration counts stand in for FP64 CG's)"}
+            line["cpu_baseline"].update(oracle_rates(w, per_it))
         print(json.dumps(line), flush=True)
     lat.close()
 
@@ -552,6 +565,7 @@ def main():
             per_it, cores = oracle_iteration_seconds(w)
             line["cpu_baseline"] = {"value": per_it * iters, "unit": "s", "cores": cores, "kind": "oracle",
                                     "sample": sample_text(w, iters, per_it)}
+            line["cpu_baseline"].update(oracle_rates(w, per_it))
         print(json.dumps(line), flush=True)
     for L in lats:
         L.close()

@@ -28,4 +28,10 @@ def test_reference_arm_json_line():
     assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["unit"] == "s"
     assert isinstance(cb["cores"], int) and 1 <= cb["cores"] <= (os.cpu_count() or 1)
     assert "t-slab" in cb["sample"]
+    # rates of the oracle: four hops per CG iteration over the 16^3 x 32 x 16 half lattice
+    assert cb["hops_per_s"] > 0 and cb["algorithmic_gbs"] > 0
+    sites = 16 * 16 * 16 * 32 // 2 * 16
+    per_it = 4.0 / cb["hops_per_s"]
+    assert abs(cb["algorithmic_gbs"] - 4 * (48 * 8 + 144 * 8 / 16) * sites / per_it / 1e9) < 1e-9 * cb["algorithmic_gbs"]
+    assert abs(d["value"] - per_it * 250) < 1e-6 * d["value"]  # 250 FP64 CG iterations on this input
     assert d["e2e"] == {"value": d["value"], "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}

@@ -4,15 +4,23 @@
 Metric: DWF solve time to a 1e-10 true residual |b - D(m) x| / |b|.  The
 headline workload is the Moebius-accelerated solve (MADWF, FP32 inner solves
 with FP64 reliable updates and FP64 defect correction) of Shamir DWF on
-24^3 x 64 x Ls=32 through a Moebius operator at Ls'=12; plain FP64 CG on the
-same GPU and input is measured beside it, and the Wilson hop (Dslash) kernel's
-achieved HBM bandwidth is reported against the measured copy peak.
+24^3 x 64 x Ls=32 through a Moebius operator at Ls'=12; plain FP64 and plain
+mixed-precision CG on the same GPU and input are measured beside it, and the
+Wilson hop (Dslash) kernel's achieved HBM bandwidth is reported against the
+measured copy peak.  The headline line also carries the 16^3 x 32 x Ls=16
+precision comparison (FP64 / FP32 / FP16-storage CG with each hop's
+bandwidth) and the 32^3 x 64 x Ls=16 four-mass ladder (multi-right-hand-side
+solve against four sequential solves).
 
 A step is one solve from a zero guess on seeded synthetic inputs already
 resident in HBM (timed with CUDA events on the solve's stream).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload madwf|mixed|hopprof|ladder]
-                  [--impl native|reference] [--no-fp64] [--no-cpu-baseline]
+                  [--impl native|reference] [--study] [--no-fp64] [--no-extras] [--no-cpu-baseline]
+
+--study (with the madwf workload) sweeps the MADWF settings (defect-correction
+passes, Pauli-Villars and Moebius tolerances, the Moebius scale b + c) and
+prints one JSON line per setting.
 
 Under torchrun (N > 1) every rank solves its own replica (no collective on
 the data path, "replicas only"); rank 0 prints the JSON line with the max
@@ -50,18 +58,18 @@ WORKLOADS = {
     # b - c = 1 and b + c = Ls / Ls' (b = 11/6, c = 5/6); 3 defect-correction passes.
     "madwf": dict(name="madwf-shamir-24^3x64-Ls32-via-mobius-Ls12", dims=(24, 24, 24, 64), Ls=32, M5=1.8,
                   m=0.002, eps=0.6, seed=3, inner="f32", madwf=True, inner_Ls=12, b=11 / 6, c=5 / 6, n_dc=3,
-                  tol_pv=1e-6, tol_mob=1e-5, sample_T=2),
+                  tol_pv=1e-6, tol_mob=1e-5, sample=(24, 24, 4, 2)),
     # 16^3 x 32 x Ls=16 Shamir, m_f = 0.01, eps = 0.5: mixed-precision CG
     "mixed": dict(name="shamir-16^3x32-Ls16-mixedCG", dims=(16, 16, 16, 32), Ls=16, M5=1.8, m=0.01, eps=0.5,
-                  seed=2, inner="f32", madwf=False, sample_T=4),
+                  seed=2, inner="f32", madwf=False, sample=(16, 16, 8, 2)),
     # the kernel-profiling case: every FP32 half-lattice field (509 MB) is larger than L2
     "hopprof": dict(name="shamir-24^3x48-Ls16-mixedCG", dims=(24, 24, 24, 48), Ls=16, M5=1.8, m=0.01, eps=0.5,
-                    seed=2, inner="f32", madwf=False, sample_T=2),
+                    seed=2, inner="f32", madwf=False, sample=(24, 24, 6, 2)),
     # Hasenbusch ladder: Moebius 32^3 x 64 x Ls=16 (b = 1.5, c = 0.5), four Gaussian sources at the
     # masses {0.001, 0.01, 0.05, 0.2}, solved together by the multi-right-hand-side CG
     "ladder": dict(name="ladder-mobius-32^3x64-Ls16-4rhs", dims=(32, 32, 32, 64), Ls=16, M5=1.8,
                    masses=(0.001, 0.01, 0.05, 0.2), m=0.001, b5=1.5, c5=0.5, eps=0.6, seed=5, inner="f32",
-                   madwf=False, ladder=True, sample_T=2),
+                   madwf=False, ladder=True, sample=(32, 32, 4, 2)),
 }
 # FP64 CG iterations to 1e-10 on each input (GB300, dwf_cg inner=f64; for the ladder
 # the summed iterations of its four mixed-precision solves); they scale the
@@ -77,7 +85,9 @@ def parse():
     ap.add_argument("--workload", default="madwf", choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--inner", default=None, choices=["f32", "f16"], help="inner precision (default per workload)")
+    ap.add_argument("--study", action="store_true", help="sweep the MADWF settings (madwf workload)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 CG comparison solve")
+    ap.add_argument("--no-extras", action="store_true", help="skip the precision comparison and the ladder")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tol", type=float, default=1e-10)
     return ap.parse_args()
@@ -212,32 +222,89 @@ def config_of(w, inner):
     return c
 
 
-# --------------------------------------------------------------------------- oracle timing
+# --------------------------------------------------------------------------- oracle timing on the host cores
+
+_SAMPLE = None  # (oracle module, EO blocks, vector) of this worker process
 
 
-def oracle_iteration_seconds(w):
-    """Seconds per FP64 oracle CG iteration (M_pc then M_pc^+) on the workload,
-    measured on a t-slab of sample_T timeslices and scaled to the full volume
-    (the oracle's work per site does not depend on the lattice extent), and the
-    host cores it kept busy: process CPU time over wall time of the timed part,
-    rounded (numpy may run its array operations on several threads)."""
-    import numpy as np
-
+def _oracle_init(spec):
+    """Worker set-up: the oracle's even-odd blocks on the sample sub-lattice."""
+    global _SAMPLE
+    sys.path.insert(0, ROOT)
     from oracle import dwf_oracle as O
     from paper_1111_5059_gb300 import inputs
 
-    X, Y, Z, T = w["dims"]
-    dims = (X, Y, Z, w["sample_T"])
-    U = inputs.gauge_field(w["seed"], dims, w["eps"])
-    b = inputs.gaussian_spinor(w["seed"], dims, w["Ls"])
-    eo = O.EO(U, w["m"], w["M5"], w["Ls"], w.get("b5", 1.0), w.get("c5", 0.0))
-    v = b * eo.even
+    U = inputs.gauge_field(spec["seed"], spec["sample"], spec["eps"])
+    b = inputs.gaussian_spinor(spec["seed"], spec["sample"], spec["Ls"])
+    eo = O.EO(U, spec["m"], spec["M5"], spec["Ls"], spec["b5"], spec["c5"])
+    _SAMPLE = (O, eo, b * eo.even)
+
+
+def _oracle_iteration(_):
+    """One FP64 oracle CG iteration's operator work (M_pc, then M_pc^+, and a
+    norm) on the sample; returns its wall and process CPU seconds."""
+    import numpy as np
+
+    O, eo, v = _SAMPLE
     t0, c0 = time.perf_counter(), time.process_time()
     q = eo.Mpc(v)
     v = eo.Mpc(q, True)
     v = v / np.sqrt(O.norm2(v))
-    wall, cpu = time.perf_counter() - t0, time.process_time() - c0
-    return wall * (T / w["sample_T"]), max(1, round(cpu / wall))
+    return time.perf_counter() - t0, time.process_time() - c0
+
+
+class OracleTimer:
+    """The FP64 oracle timed on the host's cores: one worker process per core
+    (spawned, BLAS threads 1), each running the oracle's CG-iteration work on
+    its own copy of a sub-lattice sample of the workload (the oracle's cost
+    per 5D site does not depend on the lattice extent).  A step runs one
+    iteration on every worker at once; its wall time, scaled by the full
+    volume over the volume all workers covered, is the oracle's time per
+    full-volume CG iteration on this host."""
+
+    def __init__(self, w, workers=None):
+        import multiprocessing as mp
+
+        self.w = w
+        self.workers = workers or len(os.sched_getaffinity(0))
+        spec = {"seed": w["seed"], "sample": w["sample"], "eps": w["eps"], "Ls": w["Ls"], "m": w["m"],
+                "M5": w["M5"], "b5": w.get("b5", 1.0), "c5": w.get("c5", 0.0)}
+        saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+        os.environ.update({k: "1" for k in saved})
+        try:
+            self.pool = mp.get_context("spawn").Pool(self.workers, initializer=_oracle_init, initargs=(spec,))
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+        X, Y, Z, T = w["dims"]
+        sx, sy, sz, st = w["sample"]
+        self.scale = (X * Y * Z * T) / (self.workers * sx * sy * sz * st)
+
+    def step(self):
+        """(wall seconds of one step, seconds per full-volume iteration, busy cores)."""
+        t0 = time.perf_counter()
+        res = self.pool.map(_oracle_iteration, range(self.workers), chunksize=1)
+        wall = time.perf_counter() - t0
+        busy = sum(c for _, c in res) / wall
+        return wall, wall * self.scale, max(1, round(busy))
+
+    def sample_text(self, iters, per_it):
+        X, Y, Z, T = self.w["dims"]
+        sx, sy, sz, st = self.w["sample"]
+        what = "the summed iterations of the FP64 CG solves of the ladder's masses" if self.w.get("ladder") \
+            else "the iterations of the FP64 CG solve of this input"
+        return (f"{self.workers} host cores each run one FP64 oracle CG iteration (M_pc then M_pc^+) on its own "
+                f"{sx}x{sy}x{sz}x{st}x{self.w['Ls']} sub-lattice at once; the step's wall time times "
+                f"{self.scale:.2f} (the {X}x{Y}x{Z}x{T} volume over the volume covered) gives {per_it:.1f} s per "
+                f"full-volume iteration, times {iters}, {what} (extrapolated); numpy on a host with "
+                f"{os.cpu_count()} CPUs")
+
+    def close(self):
+        self.pool.terminate()
+        self.pool.join()
 
 
 def oracle_rates(w, per_it):
@@ -252,34 +319,146 @@ def oracle_rates(w, per_it):
     return {"hops_per_s": 4.0 / per_it, "algorithmic_gbs": 4.0 * bytes_per_hop / per_it / 1e9}
 
 
-def sample_text(w, iters, per_it):
-    X, Y, Z, T = w["dims"]
-    slab = f"a {X}x{Y}x{Z}x{w['sample_T']} t-slab scaled by {T // w['sample_T']}" if w["sample_T"] < T \
-        else "the full lattice"
-    what = "the summed iterations of the FP64 CG solves of the ladder's masses" if w.get("ladder") \
-        else "the iterations of the FP64 CG solve of this input"
-    return (f"one FP64 oracle CG iteration (M_pc then M_pc^+) on {slab} ({per_it:.1f} s per full-volume "
-            f"iteration), times {iters}, {what}; numpy on a host with {os.cpu_count()} CPUs")
+def cpu_baseline(w, iters):
+    """The oracle's extrapolated solve time on the host's cores (one warm-up step, one timed)."""
+    ot = OracleTimer(w)
+    try:
+        ot.step()
+        wall, per_it, cores = ot.step()
+    finally:
+        ot.close()
+    d = {"value": per_it * iters, "unit": "s", "cores": cores, "kind": "oracle",
+         "sample": ot.sample_text(iters, per_it), "extrapolated": True, "step_seconds": wall,
+         "volume_factor": ot.scale, "iterations": iters}
+    d.update(oracle_rates(w, per_it))
+    return d
 
 
 def run_reference(args, w):
     if int(os.environ.get("RANK", "0")) != 0:
         return
-    for _ in range(args.warmup):
-        oracle_iteration_seconds(w)
-    runs = [oracle_iteration_seconds(w) for _ in range(args.steps)]
-    per_it = statistics.mean(t for t, _ in runs)
-    cores = max(c for _, c in runs)
+    ot = OracleTimer(w)
+    try:
+        for _ in range(args.warmup):
+            ot.step()
+        runs = [ot.step() for _ in range(args.steps)]
+    finally:
+        ot.close()
+    wall = statistics.mean(r[0] for r in runs)
+    per_it = statistics.mean(r[1] for r in runs)
+    cores = max(r[2] for r in runs)
     iters = FP64_ITERS[args.workload]
     value = per_it * iters
     line = {"impl": "reference", "metric": metric_name(w), "value": value, "unit": "s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_it * 1e3, "higher_is_better": False,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_of(w, "f64"),
+            "extrapolated": {"value_is": "solve time = measured step wall time x volume_factor x iterations",
+                             "step": "one oracle CG iteration on every host core's sub-lattice at once",
+                             "step_seconds": wall, "volume_factor": ot.scale, "iterations": iters,
+                             "seconds_per_full_iteration": per_it},
             "cpu_baseline": dict({"value": value, "unit": "s", "cores": cores, "kind": "oracle",
-                                  "sample": sample_text(w, iters, per_it)}, **oracle_rates(w, per_it)),
+                                  "sample": ot.sample_text(iters, per_it)}, **oracle_rates(w, per_it)),
             "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- native arm helpers
+
+
+def _events(n):
+    import torch
+
+    return [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+
+
+def roofline(kt, hbm_peak, peak_src, kernel, extra=None):
+    """Achieved algorithmic GB/s of the hop launches of one precision (CUDA
+    events around every launch) against the measured copy peak."""
+    achieved = kt["bytes"] / (kt["ms"] / 1e3) / 1e9 if kt["ms"] > 0 else None
+    r = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+         "frac": (achieved / hbm_peak) if achieved else None,
+         "frac_of_nominal_7900_gbs": (achieved / HBM_NOMINAL_GBS) if achieved else None,
+         "kernel": kernel, "launches": kt["launches"], "avg_launch_us": kt["ms"] / max(1, kt["launches"]) * 1e3,
+         "bytes_per_launch": kt["bytes"] / max(1, kt["launches"]),
+         "peak_source": ("of measured hbm_gbs (MEASURED_PEAKS.json)" if peak_src == "measured"
+                         else "of fallback 6.8 TB/s")}
+    if extra:
+        r.update(extra)
+    return r
+
+
+def precision_comparison(dev, stream, hbm_peak, peak_src, tol):
+    """16^3 x 32 x Ls=16 Shamir (m_f = 0.01, eps = 0.5): FP64, FP32 and
+    FP16-storage CG to the same true residual, with each precision's hop
+    bandwidth (one warm-up solve each, then one event-timed solve)."""
+    import torch
+
+    from paper_1111_5059_gb300 import dwf, inputs
+
+    w = WORKLOADS["mixed"]
+    U = torch.from_numpy(inputs.gauge_field(w["seed"], w["dims"], w["eps"])).to(dev)
+    b = torch.from_numpy(inputs.gaussian_spinor(w["seed"], w["dims"], w["Ls"])).to(dev)
+    lat = dwf.Lattice(w["dims"], w["Ls"], w["M5"], 1.0, 0.0, 1, stream=stream, device=dev)
+    lat.set_gauge(U)
+    x = torch.empty_like(b)
+    out = {"workload": w["name"], "lattice": "16x16x16x32", "Ls": 16, "m_f": w["m"], "tol": tol}
+    for prec in ("f64", "f32", "f16"):
+        lat.cg(w["m"], b, tol=tol, inner=prec, delta=DELTA, check_every=10, out=x)
+        lat.set_kernel_timing(True)
+        e0, e1 = _events(2)
+        e0.record(stream)
+        r = lat.cg(w["m"], b, tol=tol, inner=prec, delta=DELTA, check_every=10, out=x)
+        e1.record(stream)
+        e1.synchronize()
+        kt = lat.kernel_time(prec)
+        lat.set_kernel_timing(False)
+        kernel = "hop_kernel<f64> (FP64 Wilson hop; bound by the FP64 pipe, not HBM)" if prec == "f64" else \
+            f"hop3_kernel<{prec}> (Wilson hop at every s with fused fifth-dimension epilogues)"
+        rf = roofline(kt, hbm_peak, peak_src, kernel)
+        if prec == "f64":
+            rf["bound"] = "fp64-alu"
+        out[prec] = {"seconds": e0.elapsed_time(e1) / 1e3, "iters": r.stats["iters"],
+                     "reliable_updates": r.stats["reliable_updates"], "true_resid": r.stats["true_resid"],
+                     "hop": rf}
+    lat.close()
+    return out
+
+
+def ladder_comparison(dev, stream, tol):
+    """32^3 x 64 x Ls=16 Moebius ladder (masses {0.001, 0.01, 0.05, 0.2},
+    four Gaussian sources): the multi-right-hand-side solve (tuned in one
+    warm-up call) against the same four solves one after the other."""
+    import torch
+
+    from paper_1111_5059_gb300 import dwf, inputs
+
+    w = WORKLOADS["ladder"]
+    masses = w["masses"]
+    U = torch.from_numpy(inputs.gauge_field(w["seed"], w["dims"], w["eps"])).to(dev)
+    lat = dwf.Lattice(w["dims"], w["Ls"], w["M5"], w["b5"], w["c5"], 1, stream=stream, device=dev)
+    lat.set_gauge(U)
+    del U
+    bs = [torch.from_numpy(inputs.gaussian_spinor(w["seed"] + r, w["dims"], w["Ls"])).to(dev)
+          for r in range(len(masses))]
+    _, _, info, _ = lat.cg_multi(masses, bs, tol=tol, inner="f32", delta=DELTA, check_every=10)
+    tune_s = info["tune_seconds"]
+    e0, e1, e2 = _events(3)
+    e0.record(stream)
+    xs, st, info, _ = lat.cg_multi(masses, bs, tol=tol, inner="f32", delta=DELTA, check_every=10)
+    e1.record(stream)
+    del xs
+    seq = [lat.cg(m, bb, tol=tol, inner="f32", delta=DELTA, check_every=10) for m, bb in zip(masses, bs)]
+    e2.record(stream)
+    e2.synchronize()
+    res = {"workload": w["name"], "multi_rhs_seconds": e0.elapsed_time(e1) / 1e3,
+           "sequential_seconds": e1.elapsed_time(e2) / 1e3, "batch": info["batch"],
+           "ctas_per_sm": info["ctas_per_sm"], "autotune_seconds": tune_s,
+           "iters": [s["iters"] for s in st], "true_resid": [s["true_resid"] for s in st],
+           "sequential_iters": [r.stats["iters"] for r in seq]}
+    del seq, bs
+    lat.close()
+    return res
 
 
 # --------------------------------------------------------------------------- native arm
@@ -322,7 +501,7 @@ def run_ladder(args, w, inner, world, rank, local, dev, hbm_peak, peak_src):
     with ClockSampler(local) as clk:
         for _ in range(args.steps):
             flush.fill_(1.0)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0, e1 = _events(2)
             e0.record(stream)
             xs, st, info, _ = solve(bs)
             e1.record(stream)
@@ -342,23 +521,26 @@ def run_ladder(args, w, inner, world, rank, local, dev, hbm_peak, peak_src):
 
     # ---- e2e: sources from pinned host memory in, solutions back out, inside the timed region
     e2e = []
+    bd = [torch.empty_like(b) for b in bs]
     for _ in range(max(1, min(args.steps, 2))):
         flush.fill_(1.0)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0, e1 = _events(2)
         e0.record(stream)
-        bd = [h.to(dev, non_blocking=True) for h in b_host]
+        for d, h in zip(bd, b_host):
+            d.copy_(h, non_blocking=True)
         xs, _, _, _ = solve(bd)
         for xh, xd in zip(x_host, xs):
             xh.copy_(xd, non_blocking=True)
         e1.record(stream)
         e1.synchronize()
         e2e.append(e0.elapsed_time(e1))
-        del bd, xs
+        del xs
     e2e_ms = max_over_ranks(world, statistics.mean(e2e), dev)
+    del bd
 
     # ---- the same ladder with every right-hand side in one hop launch (no autotuning)
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0, e1 = _events(2)
     e0.record(stream)
     _, _, info_all, _ = lat.cg_multi(masses, bs, tol=args.tol, inner=inner, delta=DELTA, check_every=10,
                                      autotune=False)
@@ -368,7 +550,7 @@ def run_ladder(args, w, inner, world, rank, local, dev, hbm_peak, peak_src):
 
     # ---- the same four solves one after the other (single-RHS mixed CG)
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0, e1 = _events(2)
     e0.record(stream)
     seq = [lat.cg(m, bb, tol=args.tol, inner=inner, delta=DELTA, check_every=10) for m, bb in zip(masses, bs)]
     e1.record(stream)
@@ -379,18 +561,12 @@ def run_ladder(args, w, inner, world, rank, local, dev, hbm_peak, peak_src):
     del seq
 
     st, info = stats[-1], infos[-1]
-    achieved = kt["bytes"] / (kt["ms"] / 1e3) / 1e9 if kt["ms"] > 0 else None
-    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-            "frac": (achieved / hbm_peak) if achieved else None,
-            "frac_of_nominal_7900_gbs": (achieved / HBM_NOMINAL_GBS) if achieved else None,
-            "traffic": hop_traffic(kt["bytes"] / max(1, kt["launches"])) if inner == "f32" else None,
-            "kernel": f"hop3_kernel<{inner}> batched over right-hand sides (Wilson hop at every s, fused "
-                      "fifth-dimension epilogues per mass)",
-            "launches": kt["launches"], "avg_launch_us": kt["ms"] / max(1, kt["launches"]) * 1e3,
-            "bytes_per_launch": kt["bytes"] / max(1, kt["launches"]),
-            "timed_launches": "the eager first iteration of each batch (graph replays are not bracketed by events)",
-            "peak_source": ("of measured hbm_gbs (MEASURED_PEAKS.json)" if peak_src == "measured"
-                            else "of fallback 6.8 TB/s")}
+    roof = roofline(kt, hbm_peak, peak_src,
+                    f"hop3_kernel<{inner}> batched over right-hand sides (Wilson hop at every s, fused "
+                    "fifth-dimension epilogues per mass)",
+                    {"traffic": hop_traffic(kt["bytes"] / max(1, kt["launches"])) if inner == "f32" else None,
+                     "timed_launches": "the eager first iteration of each batch (graph replays are not bracketed "
+                                       "by events)"})
     solve_info = {"iters": [s["iters"] for s in st], "reliable_updates": [s["reliable_updates"] for s in st],
                   "op_count": [s["op_count"] for s in st], "true_resid": [s["true_resid"] for s in st],
                   "joint_iterations": info["iterations"], "batch": info["batch"], "ctas_per_sm": info["ctas_per_sm"],
@@ -407,13 +583,74 @@ def run_ladder(args, w, inner, world, rank, local, dev, hbm_peak, peak_src):
             "all_rhs_one_launch": one_launch, "clocks": clk.summary()}
     if rank == 0:
         if not args.no_cpu_baseline:
-            iters = sum(s["iters"] for s in st)
-            per_it, cores = oracle_iteration_seconds(w)
-            line["cpu_baseline"] = {"value": per_it * iters, "unit": "s", "cores": cores, "kind": "oracle",
-                                    "sample": sample_text(w, iters, per_it)
-                                    + " (the mixed solves' iteration counts stand in for FP64 CG's)"}
-            line["cpu_baseline"].update(oracle_rates(w, per_it))
+            line["cpu_baseline"] = cpu_baseline(w, sum(s["iters"] for s in st))
+            line["cpu_baseline"]["sample"] += " (the mixed solves' iteration counts stand in for FP64 CG's)"
         print(json.dumps(line), flush=True)
+    lat.close()
+
+
+def run_madwf_study(args, w, dev):
+    """MADWF settings on the headline input (Sec. 4-5: Table 1's three
+    defect-correction passes of two Pauli-Villars and one Moebius solve each,
+    Fig. 1's Moebius accuracy): one JSON line per setting with the time, the
+    paper's op counts per solve kind and the pass residuals, each solve from
+    a zero guess to the 1e-10 target; the plain mixed-precision CG is the
+    n_dc = 0 row."""
+    import torch
+
+    from paper_1111_5059_gb300 import dwf, inputs
+
+    stream = torch.cuda.current_stream(dev)
+    U = torch.from_numpy(inputs.gauge_field(w["seed"], w["dims"], w["eps"])).to(dev)
+    b = torch.from_numpy(inputs.gaussian_spinor(w["seed"], w["dims"], w["Ls"])).to(dev)
+    x = torch.empty_like(b)
+    lat = dwf.Lattice(w["dims"], w["Ls"], w["M5"], 1.0, 0.0, 1, stream=stream, device=dev)
+    lat.set_gauge(U)
+    Lp = w["inner_Ls"]
+    mobs = {}
+
+    def mobius(alpha):
+        if alpha not in mobs:
+            b5, c5 = (alpha + 1) / 2, (alpha - 1) / 2  # b - c = 1, b + c = alpha
+            mobs[alpha] = dwf.Lattice(w["dims"], Lp, w["M5"], b5, c5, 1, stream=stream, device=dev)
+            mobs[alpha].set_gauge(U)
+        return mobs[alpha]
+
+    base_alpha = w["Ls"] / Lp
+    grid = [(0, None, None, base_alpha)]
+    for n_dc in (1, 2, 3):
+        for tol_pv in (1e-4, 1e-5, 1e-6):
+            for tol_mob in (1e-3, 1e-4, 1e-5):
+                grid.append((n_dc, tol_pv, tol_mob, base_alpha))
+    for alpha in (2.0, 3.2):
+        grid.append((w["n_dc"], w["tol_pv"], w["tol_mob"], alpha))
+        grid.append((1, 1e-5, 1e-4, alpha))
+    lat.cg(w["m"], b, tol=args.tol, inner="f32", delta=DELTA, check_every=10, out=x)  # warm-up
+    for n_dc, tol_pv, tol_mob, alpha in grid:
+        e0, e1 = _events(2)
+        e0.record(stream)
+        if n_dc == 0:
+            r = lat.cg(w["m"], b, tol=args.tol, inner="f32", delta=DELTA, check_every=10, out=x)
+        else:
+            r = dwf.madwf_solve(lat, mobius(alpha), w["m"], b, n_dc=n_dc, tol_pv=tol_pv, tol_mob=tol_mob,
+                                tol_final=args.tol, inner_prec="f32", delta=DELTA, check_every=10, out=x)
+        e1.record(stream)
+        e1.synchronize()
+        row = {"study": "madwf", "n_dc": n_dc, "tol_pv": tol_pv, "tol_mob": tol_mob, "b_plus_c": alpha,
+               "seconds": e0.elapsed_time(e1) / 1e3}
+        if n_dc == 0:
+            row.update({"op_count": {"final": r.stats["op_count"], "total": r.stats["op_count"]},
+                        "iters": {"final": r.stats["iters"]}, "true_resid": r.stats["true_resid"]})
+        else:
+            st = r.stats
+            row.update({"op_count": {"pv": st["pv"]["op_count"], "mobius": st["mobius"]["op_count"],
+                                     "final": st["final_cg"]["op_count"], "total": st["total"]["op_count"]},
+                        "iters": {"pv": st["pv"]["iters"], "mobius": st["mobius"]["iters"],
+                                  "final": st["final_cg"]["iters"]},
+                        "pass_resid": st["pass_resid"], "true_resid": st["total"]["true_resid"]})
+        print(json.dumps(row), flush=True)
+    for m in mobs.values():
+        m.close()
     lat.close()
 
 
@@ -436,6 +673,11 @@ def main():
 
         build.build()
     hbm_peak, peak_src = measured_peak()
+    if args.study:
+        if not w["madwf"]:
+            raise SystemExit("--study needs the madwf workload")
+        run_madwf_study(args, w, dev)
+        return
     if w.get("ladder"):
         run_ladder(args, w, inner, world, rank, local, dev, hbm_peak, peak_src)
         if world > 1:
@@ -447,7 +689,8 @@ def main():
     U = torch.from_numpy(inputs.gauge_field(w["seed"], w["dims"], w["eps"])).to(dev)
     b_host = torch.from_numpy(inputs.gaussian_spinor(w["seed"], w["dims"], w["Ls"])).pin_memory()
     b = b_host.to(dev)
-    x_host = torch.empty_like(b_host).pin_memory()
+    x = torch.empty_like(b)
+    x_host = torch.empty(b_host.shape, dtype=b_host.dtype, pin_memory=True)
     stream = torch.cuda.current_stream(dev)
     lat = dwf.Lattice(w["dims"], w["Ls"], w["M5"], 1.0, 0.0, 1, stream=stream, device=dev)
     lat.set_gauge(U)
@@ -459,14 +702,14 @@ def main():
     del U
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    def solve(bb):
+    def solve(bb, out):
         if w["madwf"]:
             return dwf.madwf_solve(lat, mob, w["m"], bb, n_dc=w["n_dc"], tol_pv=w["tol_pv"], tol_mob=w["tol_mob"],
-                                   tol_final=args.tol, inner_prec=inner, delta=DELTA, check_every=10)
-        return lat.cg(w["m"], bb, tol=args.tol, inner=inner, delta=DELTA, check_every=10)
+                                   tol_final=args.tol, inner_prec=inner, delta=DELTA, check_every=10, out=out)
+        return lat.cg(w["m"], bb, tol=args.tol, inner=inner, delta=DELTA, check_every=10, out=out)
 
     for _ in range(args.warmup):
-        r = solve(b)
+        r = solve(b, x)
     torch.cuda.synchronize()
 
     # ---- timed region: K solves with inputs resident in HBM
@@ -479,9 +722,9 @@ def main():
     with ClockSampler(local) as clk:
         for _ in range(args.steps):
             flush.fill_(1.0)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0, e1 = _events(2)
             e0.record(stream)
-            r = solve(b)
+            r = solve(b, x)
             e1.record(stream)
             e1.synchronize()
             step_ms.append(e0.elapsed_time(e1))
@@ -499,29 +742,38 @@ def main():
     st = stats[-1]
     true_res = st["total"]["true_resid"] if w["madwf"] else st["true_resid"]
 
-    # ---- e2e: the same solve through the C ABI from pinned host buffers
+    # ---- e2e: the same solve through the public API from and to pinned host
+    # buffers (device buffers allocated beforehand: nothing is allocated in
+    # the timed region); events split it into copy-in, solve and copy-out
+    bd = torch.empty_like(b)
     e2e = []
     for _ in range(max(1, min(args.steps, 2))):
         flush.fill_(1.0)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        bd = b_host.to(dev, non_blocking=True)
-        rr = solve(bd)
-        x_host.copy_(rr.x, non_blocking=True)
-        e1.record(stream)
-        e1.synchronize()
-        e2e.append(e0.elapsed_time(e1))
-        del bd, rr
-    e2e_ms = max_over_ranks(world, statistics.mean(e2e), dev)
+        ev = _events(4)
+        ev[0].record(stream)
+        bd.copy_(b_host, non_blocking=True)
+        ev[1].record(stream)
+        solve(bd, x)
+        ev[2].record(stream)
+        x_host.copy_(x, non_blocking=True)
+        ev[3].record(stream)
+        ev[3].synchronize()
+        e2e.append([ev[0].elapsed_time(ev[3]), ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]),
+                    ev[2].elapsed_time(ev[3])])
+    del bd
+    e2e_ms = max_over_ranks(world, statistics.mean(e[0] for e in e2e), dev)
+    h2d_ms = statistics.mean(e[1] for e in e2e)
+    d2h_ms = statistics.mean(e[3] for e in e2e)
+    nbytes = b_host.numel() * 16
 
     # ---- comparisons on the same GPU: plain FP64 CG (and mixed CG for MADWF)
     comp = {}
     if not args.no_fp64:
         for name, prec in (("fp64_cg", "f64"),) + ((("mixed_cg", inner),) if w["madwf"] else ()):
             torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0, e1 = _events(2)
             e0.record(stream)
-            rf = lat.cg(w["m"], b, tol=args.tol, inner=prec, delta=DELTA, check_every=10)
+            rf = lat.cg(w["m"], b, tol=args.tol, inner=prec, delta=DELTA, check_every=10, out=x)
             e1.record(stream)
             e1.synchronize()
             secs = e0.elapsed_time(e1) / 1e3
@@ -529,18 +781,12 @@ def main():
                           "true_resid": rf.stats["true_resid"], "speedup_of_headline": secs / (ms_step / 1e3)}
             del rf
 
-    achieved = kt["bytes"] / (kt["ms"] / 1e3) / 1e9 if kt["ms"] > 0 else None
-    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-            "frac": (achieved / hbm_peak) if achieved else None,
-            "frac_of_nominal_7900_gbs": (achieved / HBM_NOMINAL_GBS) if achieved else None,
-            "traffic": hop_traffic(kt["bytes"] / max(1, kt["launches"])) if inner == "f32" else None,
-            "traffic_source": "ncu DRAM read+write per algorithmic byte on 24^3x48x16 Ls=16, scaled to this launch size",
-            "kernel": f"hop3_kernel<{inner}> (Wilson hop at every s with fused fifth-dimension epilogues)",
-            "launches": kt["launches"], "avg_launch_us": kt["ms"] / max(1, kt["launches"]) * 1e3,
-            "bytes_per_launch": kt["bytes"] / max(1, kt["launches"]),
-            "share_of_step": kt["ms"] / max(1e-9, sum(step_ms)),
-            "peak_source": ("of measured hbm_gbs (MEASURED_PEAKS.json)" if peak_src == "measured"
-                            else "of fallback 6.8 TB/s")}
+    roof = roofline(kt, hbm_peak, peak_src,
+                    f"hop3_kernel<{inner}> (Wilson hop at every s with fused fifth-dimension epilogues)",
+                    {"traffic": hop_traffic(kt["bytes"] / max(1, kt["launches"])) if inner == "f32" else None,
+                     "traffic_source": "ncu DRAM read+write per algorithmic byte on 24^3x48x16 Ls=16, scaled "
+                                       "to this launch size (null: the kernel changed since it was measured)",
+                     "share_of_step": kt["ms"] / max(1e-9, sum(step_ms))})
     if w["madwf"]:
         solve_info = {"passes": st["passes"], "pass_resid": st["pass_resid"], "true_resid": true_res,
                       "mobius_iters": st["mobius"]["iters"], "pv_iters": st["pv"]["iters"],
@@ -555,20 +801,25 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64" if inner == "f32" else "f16-storage/f32+f64",
             "data": "synthetic", "config": config_of(w, inner), "roofline": roof,
-            "e2e": {"value": e2e_ms / 1e3 / world, "unit": "s", "h2d_bytes_per_step": b_host.numel() * 16,
-                    "d2h_bytes_per_step": x_host.numel() * 16},
+            "e2e": {"value": e2e_ms / 1e3 / world, "unit": "s", "h2d_bytes_per_step": nbytes,
+                    "d2h_bytes_per_step": nbytes, "h2d_ms": h2d_ms, "solve_ms": statistics.mean(e[2] for e in e2e),
+                    "d2h_ms": d2h_ms, "h2d_gbs": nbytes / (h2d_ms / 1e3) / 1e9 if h2d_ms > 0 else None,
+                    "d2h_gbs": nbytes / (d2h_ms / 1e3) / 1e9 if d2h_ms > 0 else None},
             "gpu_launches": launches, "solve": solve_info, "clocks": clk.summary()}
     line.update(comp)
+    for L in lats:
+        L.close()
+    del b, x, flush
+    if not args.no_extras and world == 1:
+        torch.cuda.empty_cache()
+        line["precisions_16x32_Ls16"] = precision_comparison(dev, stream, hbm_peak, peak_src, args.tol)
+        torch.cuda.empty_cache()
+        line["ladder_32x64_Ls16"] = ladder_comparison(dev, stream, args.tol)
     if rank == 0:
         if not args.no_cpu_baseline:
             iters = comp["fp64_cg"]["iters"] if "fp64_cg" in comp else FP64_ITERS[args.workload]
-            per_it, cores = oracle_iteration_seconds(w)
-            line["cpu_baseline"] = {"value": per_it * iters, "unit": "s", "cores": cores, "kind": "oracle",
-                                    "sample": sample_text(w, iters, per_it)}
-            line["cpu_baseline"].update(oracle_rates(w, per_it))
+            line["cpu_baseline"] = cpu_baseline(w, iters)
         print(json.dumps(line), flush=True)
-    for L in lats:
-        L.close()
     if world > 1:
         import torch.distributed as dist
 

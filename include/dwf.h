@@ -247,9 +247,8 @@ dwf_status fgi_step(dwf_lattice_t h, int nterms, const dwf_quotient* terms, cons
                     double tau, int forecast, const dwf_cg_params* cg, dwf_stats* stats, int* fg_iters);
 
 /* dwf_apply_Mpc without any device allocation (the paper has no counterpart;
- * this serves callers that must not allocate while they run: work recorded
- * into a CUDA graph, code whose allocator owns all device memory, loops that
- * may not stall on the driver).  Same operator, arguments and boundary
+ * this serves callers that must not allocate while they run: code whose
+ * allocator owns all device memory, loops that may not stall on the driver).  Same operator, arguments and boundary
  * layout as dwf_apply_Mpc.  The handle must already exist (creation and
  * dwf_set_gauge allocate; this call does not).
  *
@@ -282,6 +281,30 @@ dwf_status dwf_apply_Mpc_noalloc(dwf_lattice_t h, double m, int dag, const void*
 dwf_status dwf_set_kernel_timing(dwf_lattice_t h, int enable);
 dwf_status dwf_get_kernel_time(dwf_lattice_t h, dwf_prec prec, double* ms, long long* launches, double* bytes);
 dwf_status dwf_get_launch_count(dwf_lattice_t h, long long* launches);
+
+/* The even-odd Schur operator M_pc (or M_pc^+ if dag != 0) of dwf_apply_Mpc
+ * (Sec. 4; same operator, mass, boundary layout and result layout: odd sites
+ * of `out` set to zero), evaluated with its fields stored at precision
+ * `prec` through the launches the solvers use for their inner iterations:
+ * M_pc = M~ B with M~ the right-preconditioned operator of dwf_cg (two
+ * Wilson hops with fused fifth-dimension epilogues).  DWF_F64 computes in
+ * FP64; DWF_F32 and DWF_F16 (FP16 storage with one FP32 scale per site and
+ * slice) compute in FP32, so the result carries the rounding of that storage
+ * (about 1e-7 and 1e-3 relative).  The input is rounded to `prec` on entry.
+ * Returns DWF_ERR_TIMEOUT if a bounded device wait of the hop kernel gave up
+ * (see dwf_set_wait_limit); the handle stays usable. */
+dwf_status dwf_apply_Mpc_prec(dwf_lattice_t h, double m, int dag, dwf_prec prec, const void* in, void* out);
+
+/* Instrumentation of the bounded device waits (no counterpart in the paper).
+ * The FP32/FP16 hop kernel waits for its asynchronous shared-memory copies
+ * on mbarriers; each wait gives up after a number of polls (default 2^22),
+ * sets the handle's error flag -- reported by the next synchronising call
+ * as DWF_ERR_TIMEOUT -- and the kernel then waits, with the default limit,
+ * for the copies it has already issued and returns.  This call sets the
+ * number of polls of the consumer waits on the handle's later launches
+ * (polls < 0 restores the default; 0 makes every consumer wait give up at
+ * once, which tests the error path without any stalled copy). */
+dwf_status dwf_set_wait_limit(dwf_lattice_t h, long long polls);
 
 #ifdef __cplusplus
 }

@@ -401,6 +401,38 @@ dwf_status solve_eo(dwf_lattice* L, double m, Field be, Field bo, Field xe, Fiel
 
 using namespace dwf;
 
+// M_pc x (or M_pc^+ x) at storage precision `prec` through the solver's own
+// hop launches: M_pc = M~ B, so M_pc x = M~ (B x) and M_pc^+ x = B^+ (M~^+ x).
+extern "C" dwf_status dwf_apply_Mpc_prec(dwf_lattice_t L, double m, int dag, dwf_prec prec, const void* in,
+                                         void* out) {
+  if (!L || !in || !out) return fail(L, DWF_ERR_INVALID_ARG, "dwf_apply_Mpc_prec: null argument");
+  if (in == out) return fail(L, DWF_ERR_INVALID_ARG, "dwf_apply_Mpc_prec: in and out must not alias");
+  if (prec < DWF_F64 || prec > DWF_F16) return fail(L, DWF_ERR_INVALID_ARG, "dwf_apply_Mpc_prec: bad precision");
+  if (!std::isfinite(m)) return fail(L, DWF_ERR_INVALID_ARG, "dwf_apply_Mpc_prec: non-finite mass");
+  if (!L->gauge_set) return fail(L, DWF_ERR_INVALID_ARG, "dwf_apply_Mpc_prec: gauge field not set");
+  dwf_status st;
+  const SOps* ops = sops_for(L, m, &st);
+  if (!ops) return st;
+  Field xe, t, ye, u;
+  DWF_TRY(field_alloc(L, "applyp.xe", prec, &xe));
+  DWF_TRY(field_alloc(L, "applyp.t", prec, &t));
+  DWF_TRY(field_alloc(L, "applyp.ye", prec, &ye));
+  DWF_TRY(field_alloc(L, "applyp.u", prec, &u));
+  DWF_TRY(launch_pack(L, in, 0, xe));
+  long long hops = 0;
+  Op o{L, ops, &hops};
+  if (!dag) {
+    DWF_TRY(launch_sop(L, xe, t, ops, SOps::B, 1.0, nullptr, 0.0));
+    DWF_TRY(apply_Mt(o, false, t, ye, u, nullptr, nullptr));
+  } else {
+    DWF_TRY(apply_Mt(o, true, xe, t, u, nullptr, nullptr));
+    DWF_TRY(launch_sop(L, t, ye, ops, SOps::BT, 1.0, nullptr, 0.0));
+  }
+  DWF_TRY(launch_unpack(L, ye, 0, out, true));
+  DWF_CUDA(L, cudaStreamSynchronize(L->stream));
+  return check_dev_err(L);
+}
+
 extern "C" dwf_status dwf_cg(dwf_lattice_t L, double m, const void* b, void* x, const dwf_cg_params* prm,
                              dwf_stats* stats) {
   if (!L || !b || !x || !prm) return fail(L, DWF_ERR_INVALID_ARG, "dwf_cg: null argument");

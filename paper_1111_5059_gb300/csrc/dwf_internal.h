@@ -17,6 +17,9 @@
 //             slot s1 = Ls of the last pair is padding and is kept zero.
 //   links   : per output parity, [Vh][8][18] reals: directions 0..3 are
 //             U_mu(n), 4..7 are U_mu(n - mu)^+, t boundary phase folded in.
+//             The FP32 pipelined kernel reads a second, direction-major copy
+//             [8][Vh][20] (links_dm), so one direction of consecutive sites
+//             is one contiguous run.
 //   nbr     : per output parity, int32 [8][Vh] half-site index of the
 //             neighbour n + mu (d < 4) or n - mu (d >= 4) on the other parity.
 #pragma once
@@ -257,6 +260,9 @@ struct dwf_lattice {
   cudaStream_t stream;
   int* nbr[2] = {nullptr, nullptr};
   void* links[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
+  // FP32 links direction-major per output parity, [8][Vh][20] floats (9 complex + 8 bytes of
+  // padding: the 80-byte rows of consecutive sites are one contiguous, 16-byte aligned copy)
+  float* links_dm[2] = {nullptr, nullptr};
   bool gauge_set = false;
   std::deque<dwf::SOps> sops;  // deque: pointers stay valid on growth
   std::map<std::string, dwf::Buffer> ws;
@@ -264,6 +270,7 @@ struct dwf_lattice {
   double* scal = nullptr;      // device scalars
   double* hscal = nullptr;     // pinned host mirror
   int* dev_err = nullptr;      // device error flag (bounded waits that gave up)
+  long wait_limit = 1L << 22;  // polls of a hop kernel's consumer wait (dwf_set_wait_limit)
   std::string err;
   // instrumentation
   long long launches = 0;  // every kernel this handle has launched
@@ -282,6 +289,7 @@ struct dwf_lattice {
 namespace dwf {
 
 constexpr int kPartials = 1 << 18;
+constexpr long kHopWaitLimit = 1L << 22;  // default polls of a bounded device wait
 constexpr int kScalars = 256;  // [0, 64): single solves; [64, 64 + 8 DWF_MAX_RHS): multi-RHS
 constexpr int kMaxBatch = 8;          // right-hand sides in one hop launch
 
@@ -316,6 +324,9 @@ dwf_status ws_get(dwf_lattice* L, const std::string& name, size_t bytes, void** 
 long field_elems(const dwf_lattice* L);                   // reals per one-parity field, incl. padding
 size_t field_bytes(const dwf_lattice* L, dwf_prec prec);  // excluding FP16 scales
 const SOps* sops_for(dwf_lattice* L, double m, dwf_status* st);
+// The structured descriptors of every fifth-dimension operator for mass m
+// (kind 0 identity, 1 structured recurrence, 2 needs the dense fallback).
+void fifth_descriptors(const dwf_params& p, int Ls, double m, SOpDesc* desc /* [SOps::NKIND] */);
 
 // one-parity field handle used by the host drivers
 struct Field {

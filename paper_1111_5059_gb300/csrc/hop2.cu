@@ -30,9 +30,13 @@
 //    recurrence of an inverse is a log-depth scan across the site's lanes by
 //    warp shuffles; odd Ls and dense fallbacks go through a shared-memory
 //    tile in the slot just consumed.
-//  * Waits on the mbarriers are bounded: a wait that gives up sets the
-//    handle's device error flag (reported as DWF_ERR_TIMEOUT), waits once more
-//    for the warp's own copies and skips the store.
+//  * Waits on the mbarriers are bounded (the consumer's limit is a launch
+//    argument, normally kWaitLimit polls): a wait that gives up sets the
+//    handle's device error flag (reported as DWF_ERR_TIMEOUT); the warp then
+//    stops at once (a warp vote makes the decision uniform), issues no
+//    further copy, waits -- with the normal limit -- for every copy it has
+//    issued and not consumed, so that no bulk copy is still writing into its
+//    shared memory when it exits, and returns.
 #include <map>
 #include <mutex>
 
@@ -44,7 +48,7 @@ namespace dwf {
 
 namespace {
 
-constexpr long kWaitLimit = 1L << 22;
+constexpr long kWaitLimit = kHopWaitLimit;
 constexpr int kSlots = 2;
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) {
@@ -70,8 +74,8 @@ __device__ __forceinline__ bool mbar_try(unsigned bar, unsigned parity) {
       : "memory");
   return ok != 0;
 }
-__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
-  for (long it = 0; it < kWaitLimit; ++it)
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, long limit = kWaitLimit) {
+  for (long it = 0; it < limit; ++it)
     if (mbar_try(bar, parity)) return true;
   return false;
 }
@@ -388,6 +392,7 @@ template <class S> struct Hop3Args {
   Ctx ctx;
   float scale, xscale;
   int* err;
+  long wait_limit;  // polls of a consumer wait before it gives up
 };
 
 template <class S> struct Pipe {
@@ -404,9 +409,9 @@ template <class S> struct Pipe {
 // the group's links) or d = 8, the group's own blocks of the site term.  The
 // group's neighbour indices and links sit in buffer lb.
 template <class S, int NST>
-__device__ __forceinline__ void issue_stage(const Pipe<S>& P, long g, int t, int slot, int lb) {
+__device__ __forceinline__ bool issue_stage(const Pipe<S>& P, long g, int t, int slot, int lb) {
   const Hop3Args<S>& a = *P.a;
-  if (g >= a.ngroups) return;
+  if (g >= a.ngroups) return false;  // past the CTA's last group: nothing issued
   const int r = t / NST, d = t - r * NST;
   const long h0 = g * a.G;
   const long left = a.Vh - h0;
@@ -458,6 +463,7 @@ __device__ __forceinline__ void issue_stage(const Pipe<S>& P, long g, int t, int
       bulk_g2s(smem_addr(dst + G * P.blk), reinterpret_cast<const unsigned char*>(src.norm) + h0 * P.sblk,
                nact * P.sblk, bar);
   }
+  return true;
 }
 
 // (re, im) of pair j of slot block bi
@@ -547,8 +553,9 @@ __global__ void __launch_bounds__(32, 12) hop3_kernel(const Hop3Args<S> a) {
   };
   long g = blockIdx.x;
   load_nb(g, 0);
+  unsigned issued = 0;  // stages issued so far (issue order = consumption order)
 #pragma unroll
-  for (int s = 0; s < kSlots; ++s) issue_stage<S, NST>(P, g, s, s, 0);
+  for (int s = 0; s < kSlots; ++s) issued += issue_stage<S, NST>(P, g, s, s, 0);
   unsigned seq = 0;  // global index of the stage being consumed; slot seq % kSlots
   bool bad = false;
   double part = 0.0;
@@ -571,7 +578,10 @@ __global__ void __launch_bounds__(32, 12) hop3_kernel(const Hop3Args<S> a) {
       const int d = t - r * NST;
       const int slot = seq % kSlots;
       unsigned char* sl = sm + slot * a.ctx.slot_bytes;
-      if (!mbar_wait(P.bar0 + 8u * slot, (seq / kSlots) & 1)) bad = true;
+      if (__any_sync(0xffffffffu, !mbar_wait(P.bar0 + 8u * slot, (seq / kSlots) & 1, a.wait_limit))) {
+        bad = true;
+        break;
+      }
       float2 xr[12], xi[12];  // the site term (d = 8)
       if (d < 8) {
         if (act) {
@@ -597,9 +607,9 @@ __global__ void __launch_bounds__(32, 12) hop3_kernel(const Hop3Args<S> a) {
       const int k2 = t + kSlots;
       if (!last) {
         if (k2 < NSG)
-          issue_stage<S, NST>(P, g, k2, slot, lb);
+          issued += issue_stage<S, NST>(P, g, k2, slot, lb);
         else
-          issue_stage<S, NST>(P, g + stride, k2 - NSG, slot, lb ^ 1);
+          issued += issue_stage<S, NST>(P, g + stride, k2 - NSG, slot, lb ^ 1);
       }
       ++seq;
       if (last) {
@@ -625,9 +635,9 @@ __global__ void __launch_bounds__(32, 12) hop3_kernel(const Hop3Args<S> a) {
         if (eout.kind != 0) sop_pair(eout, ar, ai, tile, bi, j, act, G, nact, Ls, Lh);
         // the delayed refill of the tile's slot
         if (k2 < NSG)
-          issue_stage<S, NST>(P, g, k2, slot, lb);
+          issued += issue_stage<S, NST>(P, g, k2, slot, lb);
         else
-          issue_stage<S, NST>(P, g + stride, k2 - NSG, slot, lb ^ 1);
+          issued += issue_stage<S, NST>(P, g + stride, k2 - NSG, slot, lb ^ 1);
         if (2 * j + 1 >= Ls) {  // odd Ls: the padding slot stays zero
 #pragma unroll
           for (int k = 0; k < 12; ++k) {
@@ -635,7 +645,7 @@ __global__ void __launch_bounds__(32, 12) hop3_kernel(const Hop3Args<S> a) {
             ai[k].y = 0.f;
           }
         }
-        if (act && !bad) {
+        if (act) {
           store_pair(a.out[r], h0 + i, j, Lh, ar, ai);
           float2 p0 = make_float2(0.f, 0.f), p1 = p0;
 #pragma unroll
@@ -656,10 +666,14 @@ __global__ void __launch_bounds__(32, 12) hop3_kernel(const Hop3Args<S> a) {
         }
       }
     }
+    if (bad) break;
   }
   if (bad) {
+    // stages seq .. issued - 1 are in flight: wait (normal limit) for each
+    // before the CTA's shared memory is released
     if (lane == 0) atomicExch(a.err, 1);
-    for (int s = 0; s < kSlots; ++s) mbar_wait(P.bar0 + 8u * s, ((seq + s) / kSlots) & 1);  // bounded
+    for (unsigned q = seq; q < issued; ++q) mbar_wait(P.bar0 + 8u * (q % kSlots), (q / kSlots) & 1);
+    return;
   }
   if (a.partials[0]) {
     // per right-hand side: sum the lanes (i, j) in a fixed order
@@ -671,6 +685,393 @@ __global__ void __launch_bounds__(32, 12) hop3_kernel(const Hop3Args<S> a) {
       double t = 0.0;
       for (int q = 0; q < G * Lh; ++q) t += sp[lane * 32 + q];
       a.partials[lane][blockIdx.x] = t;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- the FP32 fast path
+//
+// Single right-hand side, FP32 storage, even Ls with structured fifth-dimension
+// operators, Lh (and so G = 32 / Lh) fixed at compile time.  Differences from
+// hop3_kernel, each measured on GB300:
+//  * a direction stage carries its G sites' links for that direction (one
+//    contiguous copy from the direction-major link array), so no per-group link
+//    buffer is kept and the warp's shared memory is two slots plus the
+//    neighbour indices;
+//  * a slot is refilled as soon as its data are in registers: the neighbour
+//    spinor is spin-projected straight out of shared memory into the 6-complex
+//    half spinor and the direction's links are loaded, then the copy for the
+//    stage two ahead is issued, before the SU(3) products;
+//  * the site term, if any, is the group's first stage: its fifth-dimension
+//    operator runs on it at once and it seeds the accumulator (scaled by
+//    xscale / scale, the hop sum is scaled at the end);
+//  * compile-time Lh turns the slot addressing into immediates and unrolls the
+//    epilogue's scan; the epilogue's per-lane powers of rho are computed once.
+
+// psi projected by (1 - sg g_MU) straight from the slot block of this lane's
+// site (chunk j of each complex component)
+template <int MU>
+__device__ __forceinline__ void project_smem(float sg, const float4* c4, int j, int Lh, float2* hr, float2* hi) {
+  typedef Proj<MU, 1> P;
+  const float2 sgp = f2(sg);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float4 v0 = c4[a * Lh + j], v1 = c4[(P::J1 * 3 + a) * Lh + j];
+    cpair_s<P::C1R, P::C1I>(sgp, make_float2(v0.x, v0.y), make_float2(v0.z, v0.w), make_float2(v1.x, v1.y),
+                            make_float2(v1.z, v1.w), hr[a], hi[a]);
+    const float4 v2 = c4[(3 + a) * Lh + j], v3 = c4[(P::J2 * 3 + a) * Lh + j];
+    cpair_s<P::C2R, P::C2I>(sgp, make_float2(v2.x, v2.y), make_float2(v2.z, v2.w), make_float2(v3.x, v3.y),
+                            make_float2(v3.z, v3.w), hr[3 + a], hi[3 + a]);
+  }
+}
+
+// acc += (1 - sg g_MU) U psi given the projected half spinor h = (hr, hi)
+template <int MU>
+__device__ __forceinline__ void su3_accumulate(float sg, const float2* hr, const float2* hi, const float2* U,
+                                               float2* ar, float2* ai) {
+  typedef Proj<MU, 1> P;
+  const float2 sgp = f2(sg);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    float2 ur[3], ui[3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      ur[b] = f2(U[3 * a + b].x);
+      ui[b] = f2(U[3 * a + b].y);
+    }
+#pragma unroll
+    for (int hh = 0; hh < 2; ++hh) {
+      float2 A = make_float2(0.f, 0.f), B = A, C = A, D = A;
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        A = fma2(ur[b], hr[3 * hh + b], A);
+        B = fma2(ui[b], hi[3 * hh + b], B);
+        C = fma2(ur[b], hi[3 * hh + b], C);
+        D = fma2(ui[b], hr[3 * hh + b], D);
+      }
+      const float2 gr = fma2(f2(-1.f), B, A), gi = add2(C, D);
+      ar[3 * hh + a] = add2(ar[3 * hh + a], gr);
+      ai[3 * hh + a] = add2(ai[3 * hh + a], gi);
+      if (hh == P::S2) {
+        float2 zr, zi;
+        cpair_s<P::D2R, P::D2I>(sgp, ar[6 + a], ai[6 + a], gr, gi, zr, zi);
+        ar[6 + a] = zr;
+        ai[6 + a] = zi;
+      }
+      if (hh == P::S3) {
+        float2 zr, zi;
+        cpair_s<P::D3R, P::D3I>(sgp, ar[9 + a], ai[9 + a], gr, gi, zr, zi);
+        ar[9 + a] = zr;
+        ai[9 + a] = zi;
+      }
+    }
+  }
+}
+
+// rho^(2j) and rho^(2(LH-1-j)) of this lane's pair j (computed once per launch)
+template <int LH>
+__device__ __forceinline__ float2 lane_powers(const SOpK<float>& op, int j) {
+  float a = 1.f, b = 1.f;
+  if (op.has_inv) {
+    const float r2 = op.rho * op.rho;
+#pragma unroll
+    for (int q = 0; q < LH; ++q) {
+      if (q < j) a *= r2;
+      if (q > j) b *= r2;
+    }
+  }
+  return make_float2(a, b);
+}
+
+// sop_shfl with Lh fixed at compile time and the lane powers given
+template <int LH>
+__device__ __forceinline__ void sop_reg(const SOpK<float>& op, float2 pw, float2* re, float2* im, int j) {
+  const int lane = threadIdx.x, base = lane - j;
+  const float rho = op.rho, m = op.m;
+  const float wk = op.has_inv ? -rho * m * (op.c0 / op.ginv) : 0.f;
+#pragma unroll
+  for (int half = 0; half < 2; ++half) {
+    const int up = half ^ op.trans;
+    float2 A[6], B[6];
+    const float2 gi = f2(op.ginv);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const int kk = 6 * half + k;
+      A[k] = mul2(gi, make_float2(re[kk].x, im[kk].x));
+      B[k] = mul2(gi, make_float2(re[kk].y, im[kk].y));
+    }
+    if (op.has_inv) {
+      const float2 r1 = f2(rho);
+      if (!up) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) B[k] = fma2(r1, A[k], B[k]);
+        float rd = rho * rho;
+#pragma unroll
+        for (int d = 1; d < LH; d <<= 1) {
+          const bool ok = j >= d;
+          const int src = ok ? lane - d : lane;
+          const float2 f = f2(ok ? rd : 0.f);
+#pragma unroll
+          for (int k = 0; k < 6; ++k) B[k] = fma2(f, shfl2(B[k], src), B[k]);
+          rd *= rd;
+        }
+        const int src = j > 0 ? lane - 1 : lane;
+        const float2 f = f2(j > 0 ? rho : 0.f);
+        const float2 wa = f2(wk * pw.x), wb = f2(wk * pw.x * rho);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+          A[k] = fma2(f, shfl2(B[k], src), A[k]);
+          const float2 w = shfl2(B[k], base + LH - 1);
+          A[k] = fma2(wa, w, A[k]);
+          B[k] = fma2(wb, w, B[k]);
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) A[k] = fma2(r1, B[k], A[k]);
+        float rd = rho * rho;
+#pragma unroll
+        for (int d = 1; d < LH; d <<= 1) {
+          const bool ok = j + d < LH;
+          const int src = ok ? lane + d : lane;
+          const float2 f = f2(ok ? rd : 0.f);
+#pragma unroll
+          for (int k = 0; k < 6; ++k) A[k] = fma2(f, shfl2(A[k], src), A[k]);
+          rd *= rd;
+        }
+        const int src = j < LH - 1 ? lane + 1 : lane;
+        const float2 f = f2(j < LH - 1 ? rho : 0.f);
+        const float2 wa = f2(wk * pw.y * rho), wb = f2(wk * pw.y);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+          B[k] = fma2(f, shfl2(A[k], src), B[k]);
+          const float2 w = shfl2(A[k], base);
+          A[k] = fma2(wa, w, A[k]);
+          B[k] = fma2(wb, w, B[k]);
+        }
+      }
+    }
+    const float2 g1 = f2(op.g1), d1 = f2(op.d1);
+    const bool edge = up ? (j == LH - 1) : (j == 0);
+    const int src = up ? (edge ? base : lane + 1) : (edge ? base + LH - 1 : lane - 1);
+    const float2 fe = f2(edge ? -m : 1.f);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const int kk = 6 * half + k;
+      float2 ya, yb;
+      if (!up) {
+        const float2 q = mul2(fe, shfl2(B[k], src));
+        ya = fma2(d1, q, mul2(g1, A[k]));
+        yb = fma2(d1, A[k], mul2(g1, B[k]));
+      } else {
+        const float2 q = mul2(fe, shfl2(A[k], src));
+        ya = fma2(d1, B[k], mul2(g1, A[k]));
+        yb = fma2(d1, q, mul2(g1, B[k]));
+      }
+      re[kk] = make_float2(ya.x, yb.x);
+      im[kk] = make_float2(ya.y, yb.y);
+    }
+  }
+}
+
+struct HopFArgs {
+  const float* in;
+  float* out;
+  const float* x;
+  SOpK<float> ex, eout;
+  const float* links_dm;  // [8][Vh][20]
+  const int* nbr;         // [8][Vh]
+  double* partials;       // one double per CTA (or null)
+  long Vh, ngroups;
+  float scale, xfold;     // xfold = xscale / scale
+  int* err;
+  long wait_limit;
+};
+
+template <int LH> struct HopFShape {
+  static constexpr int G = 32 / LH;
+  static constexpr int BLK = 12 * LH * 16;                       // one site's FP32 spinor block
+  static constexpr int LK_OFF = G * BLK;                         // the links of the stage's direction
+  static constexpr int SLOT = (LK_OFF + G * 80 + 127) / 128 * 128;
+  static constexpr int NB_OFF = 2 * SLOT;                        // neighbour indices [2 groups][8][G]
+  static constexpr int SMEM = NB_OFF + 2 * 8 * G * 4;
+};
+
+template <int LH, int DAG, int HX, int MINB>
+__global__ void __launch_bounds__(32, MINB) hopf_kernel(const HopFArgs a) {
+  typedef HopFShape<LH> Sh;
+  constexpr int G = Sh::G, BLK = Sh::BLK, SLOT = Sh::SLOT;
+  constexpr int NST = HX ? 9 : 8;  // stages per group (HX: the site term first)
+  extern __shared__ __align__(128) unsigned char sm[];
+  __shared__ __align__(8) unsigned long long bars[2];
+  __shared__ double red[32];
+  const int lane = threadIdx.x;
+  const int i = lane / LH;
+  const int j = lane - i * LH;
+  int* nbs = reinterpret_cast<int*>(sm + Sh::NB_OFF);
+  const unsigned bar0 = smem_addr(&bars[0]);
+  if (lane == 0) {
+    mbar_init(bar0, 1);
+    mbar_init(bar0 + 8u, 1);
+    fence_async_smem();
+  }
+  __syncwarp();
+  const float2 pw_ex = HX ? lane_powers<LH>(a.ex, j) : make_float2(1.f, 1.f);
+  const float2 pw_eo = lane_powers<LH>(a.eout, j);
+  const long stride = gridDim.x;
+  // neighbour indices of group g into buffer lb (each lane reads back only what it wrote)
+  auto load_nb = [&](long g, int lb) {
+    if (lane < G) {
+      const long hh = g * G + lane;
+      const bool ok = g < a.ngroups && hh < a.Vh;
+#pragma unroll
+      for (int d = 0; d < 8; ++d) nbs[(lb * 8 + d) * G + lane] = ok ? __ldg(a.nbr + (long)d * a.Vh + hh) : 0;
+    }
+  };
+  // stage t of group g into slot `slot`; returns whether anything was issued
+  auto issue = [&](long g, int t, int slot, int lb) -> bool {
+    if (g >= a.ngroups) return false;
+    const long h0 = g * G;
+    const long left = a.Vh - h0;
+    const int nact = left < G ? (int)left : G;
+    const unsigned bar = bar0 + 8u * slot;
+    unsigned char* dst = sm + slot * SLOT;
+    const int d = HX ? t - 1 : t;
+    fence_async_smem();  // earlier generic reads of this slot before the copies
+    const unsigned bytes = nact * BLK + (d >= 0 ? nact * 80 : 0);
+    if (lane == 0) mbar_expect_tx(bar, bytes);
+    __syncwarp();
+    if (d >= 0) {
+      const int nb_k = lane < G ? nbs[(lb * 8 + d) * G + lane] : 0;
+      const int nb0 = __shfl_sync(0xffffffffu, nb_k, 0);
+      const unsigned run = __ballot_sync(0xffffffffu, lane >= nact || nb_k == nb0 + lane);
+      if (run == 0xffffffffu) {
+        if (lane == 0)
+          bulk_g2s(smem_addr(dst), reinterpret_cast<const unsigned char*>(a.in) + (long)nb0 * BLK, nact * BLK, bar);
+      } else if (lane < nact) {
+        bulk_g2s(smem_addr(dst + lane * BLK), reinterpret_cast<const unsigned char*>(a.in) + (long)nb_k * BLK, BLK,
+                 bar);
+      }
+      if (lane == 0) bulk_g2s(smem_addr(dst + Sh::LK_OFF), a.links_dm + ((long)d * a.Vh + h0) * 20, nact * 80, bar);
+    } else if (lane == 0) {
+      bulk_g2s(smem_addr(dst), reinterpret_cast<const unsigned char*>(a.x) + h0 * BLK, nact * BLK, bar);
+    }
+    return true;
+  };
+  long g = blockIdx.x;
+  load_nb(g, 0);
+  unsigned issued = 0;  // stages issued so far (issue order = consumption order)
+  issued += issue(g, 0, 0, 0);
+  issued += issue(g, 1, 1, 0);
+  unsigned seq = 0;  // the stage being consumed: slot seq & 1, phase (seq >> 1) & 1
+  bool bad = false;
+  double part = 0.0;
+  int lb = 0;
+  for (; g < a.ngroups; g += stride, lb ^= 1) {
+    load_nb(g + stride, lb ^ 1);
+    const long h0 = g * G;
+    const long left = a.Vh - h0;
+    const int nact = left < G ? (int)left : G;
+    const bool act = i < nact;
+    float2 ar[12], ai[12];
+    if (!HX) {
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        ar[k] = make_float2(0.f, 0.f);
+        ai[k] = ar[k];
+      }
+    }
+#pragma unroll 1
+    for (int t = 0; t < NST; ++t) {
+      const int slot = seq & 1;
+      const unsigned char* sl = sm + slot * SLOT;
+      if (__any_sync(0xffffffffu, !mbar_wait(bar0 + 8u * slot, (seq >> 1) & 1, a.wait_limit))) {
+        bad = true;
+        break;
+      }
+      const int k2 = t + 2;
+      const int d = HX ? t - 1 : t;
+      if (d < 0) {
+        // the site term seeds the accumulator: xfold * Ex x
+        const float4* c4 = reinterpret_cast<const float4*>(sl + i * BLK) + j;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+          const float4 v = act ? c4[k * LH] : make_float4(0.f, 0.f, 0.f, 0.f);
+          ar[k] = make_float2(v.x, v.y);
+          ai[k] = make_float2(v.z, v.w);
+        }
+        __syncwarp();
+        issued += k2 < NST ? issue(g, k2, slot, lb) : issue(g + stride, k2 - NST, slot, lb ^ 1);
+        if (a.ex.kind != 0) sop_reg<LH>(a.ex, pw_ex, ar, ai, j);
+        const float2 xf = f2(a.xfold);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+          ar[k] = mul2(xf, ar[k]);
+          ai[k] = mul2(xf, ai[k]);
+        }
+      } else {
+        // (1 -+ g_mu) sign: +1 forward / -1 backward, flipped by the dagger
+        const float sg = ((d < 4) != (DAG != 0)) ? 1.f : -1.f;
+        float2 hr[6], hi[6], U[9];
+        if (act) {
+          const float4* c4 = reinterpret_cast<const float4*>(sl + i * BLK);
+          switch (d & 3) {
+            case 0: project_smem<0>(sg, c4, j, LH, hr, hi); break;
+            case 1: project_smem<1>(sg, c4, j, LH, hr, hi); break;
+            case 2: project_smem<2>(sg, c4, j, LH, hr, hi); break;
+            default: project_smem<3>(sg, c4, j, LH, hr, hi); break;
+          }
+          const float2* u = reinterpret_cast<const float2*>(sl + Sh::LK_OFF + i * 80);
+#pragma unroll
+          for (int e = 0; e < 9; ++e) U[e] = u[e];
+        }
+        __syncwarp();
+        issued += k2 < NST ? issue(g, k2, slot, lb) : issue(g + stride, k2 - NST, slot, lb ^ 1);
+        if (act) {
+          switch (d & 3) {
+            case 0: su3_accumulate<0>(sg, hr, hi, U, ar, ai); break;
+            case 1: su3_accumulate<1>(sg, hr, hi, U, ar, ai); break;
+            case 2: su3_accumulate<2>(sg, hr, hi, U, ar, ai); break;
+            default: su3_accumulate<3>(sg, hr, hi, U, ar, ai); break;
+          }
+        }
+      }
+      ++seq;
+    }
+    if (bad) break;
+    const float2 sc = f2(a.scale);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      ar[k] = mul2(sc, ar[k]);
+      ai[k] = mul2(sc, ai[k]);
+    }
+    if (a.eout.kind != 0) sop_reg<LH>(a.eout, pw_eo, ar, ai, j);
+    if (act) {
+      store_pair(FieldRef<float>{a.out, nullptr}, h0 + i, j, LH, ar, ai);
+      if (a.partials) {
+        float2 p0 = make_float2(0.f, 0.f), p1 = p0;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+          p0 = fma2(ar[k], ar[k], p0);
+          p1 = fma2(ai[k], ai[k], p1);
+        }
+        part += (double)((p0.x + p0.y) + (p1.x + p1.y));
+      }
+    }
+  }
+  if (bad) {
+    // stages seq .. issued - 1 are in flight: wait (normal limit) for each
+    // before the CTA's shared memory is released
+    if (lane == 0) atomicExch(a.err, 1);
+    for (unsigned q = seq; q < issued; ++q) mbar_wait(bar0 + 8u * (q & 1), (q >> 1) & 1);
+    return;
+  }
+  if (a.partials) {
+    red[lane] = part;
+    __syncwarp();
+    if (lane == 0) {
+      double t = 0.0;
+      for (int q = 0; q < 32; ++q) t += red[q];  // fixed order
+      a.partials[blockIdx.x] = t;
     }
   }
 }
@@ -738,6 +1139,7 @@ static dwf_status hop3_t(dwf_lattice* L, const HopCall& c, const HopBatch& b, co
   a.scale = (float)c.scale;
   a.xscale = (float)c.xscale;
   a.err = L->dev_err;
+  a.wait_limit = L->wait_limit;
   const size_t smem = (size_t)a.ctx.total;
   auto run = [&](auto kern) -> dwf_status {
     DWF_CUDA(L, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -760,8 +1162,65 @@ static dwf_status hop3_t(dwf_lattice* L, const HopCall& c, const HopBatch& b, co
   return c.has_x ? run(hop3_kernel<S, 0, 1, 0>) : run(hop3_kernel<S, 0, 0, 0>);
 }
 
+// The FP32 fast path takes one right-hand side, even Ls with Lh in {4, 6, 8, 16,
+// 32} and structured fifth-dimension operators.
+static bool hopf_takes(const dwf_lattice* L, const HopCall& c, const HopBatch& b, const SOpK<float>& ex,
+                       const SOpK<float>& eout) {
+  if (b.nrhs != 1 || b.in[0].prec != DWF_F32 || (L->Ls & 1) || !L->links_dm[c.out_parity]) return false;
+  if (L->Lh != 4 && L->Lh != 6 && L->Lh != 8 && L->Lh != 16 && L->Lh != 32) return false;
+  if (c.has_x && (ex.kind == 2 || c.scale == 0.0)) return false;
+  return eout.kind != 2;
+}
+
+template <int LH, int MINB>
+static dwf_status hopf_t(dwf_lattice* L, const HopCall& c, const HopBatch& b, const SOpK<float>& ex,
+                         const SOpK<float>& eout, int ctas_per_sm) {
+  typedef HopFShape<LH> Sh;
+  HopFArgs a{};
+  a.in = reinterpret_cast<const float*>(b.in[0].v);
+  a.out = reinterpret_cast<float*>(b.out[0].v);
+  a.x = c.has_x ? reinterpret_cast<const float*>(b.x[0].v) : nullptr;
+  if (c.has_x) a.ex = ex;
+  a.eout = eout;
+  a.links_dm = L->links_dm[c.out_parity];
+  a.nbr = L->nbr[c.out_parity];
+  a.partials = b.partials[0];
+  a.Vh = L->Vh;
+  a.ngroups = (L->Vh + Sh::G - 1) / Sh::G;
+  a.scale = (float)c.scale;
+  a.xfold = c.has_x ? (float)(c.xscale / c.scale) : 0.f;
+  a.err = L->dev_err;
+  a.wait_limit = L->wait_limit;
+  auto run = [&](auto kern) -> dwf_status {
+    DWF_CUDA(L, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Sh::SMEM));
+    int per = 0, sms = 0;
+    if (resident_per_sm(reinterpret_cast<const void*>(kern), Sh::SMEM, &per, &sms))
+      return fail(L, DWF_ERR_CUDA, "hop: occupancy query failed");
+    if (ctas_per_sm > 0 && ctas_per_sm < per) per = ctas_per_sm;
+    const long resident = (long)per * sms;
+    const long grid = a.ngroups < resident ? a.ngroups : resident;  // persistent: one wave
+    if (b.partials[0] && grid > kPartials) return fail(L, DWF_ERR_INVALID_ARG, "partial-sum buffer too small");
+    kern<<<(unsigned)grid, 32, Sh::SMEM, L->stream>>>(a);
+    if (c.nblocks) *c.nblocks = (int)grid;
+    return DWF_OK;
+  };
+  if (c.dag) return c.has_x ? run(hopf_kernel<LH, 1, 1, MINB>) : run(hopf_kernel<LH, 1, 0, MINB>);
+  return c.has_x ? run(hopf_kernel<LH, 0, 1, MINB>) : run(hopf_kernel<LH, 0, 0, MINB>);
+}
+
 dwf_status launch_hop2(dwf_lattice* L, const HopCall& c, const HopBatch& b, const SOpK<float>* ex,
                        const SOpK<float>* eout, int G, int ctas_per_sm) {
+  if (hopf_takes(L, c, b, ex[0], eout[0])) {
+    // resident warps per SM as measured best on GB300: 16 (128 registers) for
+    // Lh = 6 and 8, 12 (168 registers) where the epilogue scan is longer
+    switch (L->Lh) {
+      case 4: return hopf_t<4, 12>(L, c, b, ex[0], eout[0], ctas_per_sm);
+      case 6: return hopf_t<6, 16>(L, c, b, ex[0], eout[0], ctas_per_sm);
+      case 8: return hopf_t<8, 16>(L, c, b, ex[0], eout[0], ctas_per_sm);
+      case 16: return hopf_t<16, 12>(L, c, b, ex[0], eout[0], ctas_per_sm);
+      default: return hopf_t<32, 12>(L, c, b, ex[0], eout[0], ctas_per_sm);
+    }
+  }
   if (b.in[0].prec == DWF_F32) return hop3_t<float>(L, c, b, ex, eout, G, ctas_per_sm);
   return hop3_t<__half>(L, c, b, ex, eout, G, ctas_per_sm);
 }

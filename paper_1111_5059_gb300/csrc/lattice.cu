@@ -158,6 +158,38 @@ void shifts(int Ls, double m, Mat* up, Mat* dn) {
 }
 }  // namespace
 
+void fifth_descriptors(const dwf_params& p, int Ls, double m, SOpDesc* desc) {
+  // y = (g1 + d1 Q)(g2 + d2 Q)^-1 x with A = alpha + beta Q, B = b + c Q,
+  // alpha = (4-M5) b + 1, beta = (4-M5) c - 1.
+  const double b = p.b, c = p.c, w = 4.0 - p.M5;
+  const double al = w * b + 1.0, be = w * c - 1.0;
+  const double f[SOps::NKIND][4] = {
+      {al, be, 1, 0}, {al, be, 1, 0},  // A, AT
+      {1, 0, al, be}, {1, 0, al, be},  // AINV, AINVT
+      {b, c, 1, 0},   {b, c, 1, 0},    // B, BT
+      {1, 0, b, c},   {1, 0, b, c},    // BINV, BINVT
+      {b, c, al, be}, {b, c, al, be},  // E1 = B A^-1, E1T
+      {al, be, b, c}, {al, be, b, c},  // E0 = A B^-1, E0T
+  };
+  for (int k = 0; k < SOps::NKIND; ++k) {
+    SOpDesc& d = desc[k];
+    const double g1 = f[k][0], d1 = f[k][1], g2 = f[k][2], d2 = f[k][3];
+    d.trans = k & 1;
+    d.dense_kind = k;
+    d.g1 = g1;
+    d.d1 = d1;
+    d.m = m;
+    d.has_inv = d2 != 0.0;
+    d.ginv = 1.0 / g2;
+    d.rho = -d2 / g2;
+    const double den = 1.0 + m * std::pow(d.rho, Ls);
+    d.c0 = 1.0 / (g2 * den);
+    const bool identity = g1 == 1.0 && d1 == 0.0 && g2 == 1.0 && d2 == 0.0;
+    const bool stable = g2 != 0.0 && (!d.has_inv || (std::fabs(d.rho) <= 1.0 && std::fabs(den) > 1e-8));
+    d.kind = identity ? 0 : (stable ? 1 : 2);
+  }
+}
+
 const SOps* sops_for(dwf_lattice* L, double m, dwf_status* st) {
   *st = DWF_OK;
   for (auto& o : L->sops)
@@ -200,36 +232,7 @@ const SOps* sops_for(dwf_lattice* L, double m, dwf_status* st) {
   std::vector<float> hf(host.begin(), host.end());
   SOps o;
   o.m = m;
-  // Structured descriptors: y = (g1 + d1 Q)(g2 + d2 Q)^-1 x with
-  // A = alpha + beta Q, B = b + c Q, alpha = (4-M5) b + 1, beta = (4-M5) c - 1.
-  {
-    const double al = w * b + 1.0, be = w * c - 1.0;
-    const double f[SOps::NKIND][4] = {
-        {al, be, 1, 0}, {al, be, 1, 0},  // A, AT
-        {1, 0, al, be}, {1, 0, al, be},  // AINV, AINVT
-        {b, c, 1, 0},   {b, c, 1, 0},    // B, BT
-        {1, 0, b, c},   {1, 0, b, c},    // BINV, BINVT
-        {b, c, al, be}, {b, c, al, be},  // E1 = B A^-1, E1T
-        {al, be, b, c}, {al, be, b, c},  // E0 = A B^-1, E0T
-    };
-    for (int k = 0; k < SOps::NKIND; ++k) {
-      SOpDesc& d = o.desc[k];
-      const double g1 = f[k][0], d1 = f[k][1], g2 = f[k][2], d2 = f[k][3];
-      d.trans = k & 1;
-      d.dense_kind = k;
-      d.g1 = g1;
-      d.d1 = d1;
-      d.m = m;
-      d.has_inv = d2 != 0.0;
-      d.ginv = 1.0 / g2;
-      d.rho = -d2 / g2;
-      const double den = 1.0 + m * std::pow(d.rho, n);
-      d.c0 = 1.0 / (g2 * den);
-      const bool identity = g1 == 1.0 && d1 == 0.0 && g2 == 1.0 && d2 == 0.0;
-      const bool stable = !d.has_inv || (std::fabs(d.rho) <= 1.0 && std::fabs(den) > 1e-8);
-      d.kind = identity ? 0 : (stable ? 1 : 2);
-    }
-  }
+  fifth_descriptors(L->p, n, m, o.desc);
   if (cudaMalloc(&o.d64, host.size() * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&o.d32, hf.size() * sizeof(float)) != cudaSuccess) {
     *st = fail(L, DWF_ERR_OOM, "s-op matrices");
@@ -381,6 +384,20 @@ dwf_status launch_unpack(dwf_lattice* L, Field in, int parity, void* bnd, bool z
   return DWF_OK;
 }
 
+// [Vh][8][18] -> [8][Vh][20] (the FP32 direction-major copy)
+__global__ void links_direction_major(const float* __restrict__ src, float* __restrict__ dst, long Vh) {
+  const long q = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= Vh * 8) return;
+  const long h = q >> 3;
+  const int d = (int)(q & 7);
+  const float* s = src + (h * 8 + d) * 18;
+  float* o = dst + ((long)d * Vh + h) * 20;
+#pragma unroll
+  for (int e = 0; e < 18; ++e) o[e] = s[e];
+  o[18] = 0.f;
+  o[19] = 0.f;
+}
+
 dwf_status launch_pack_gauge(dwf_lattice* L, const void* U) {
   const size_t per = (size_t)L->Vh * 8 * 18;
   const size_t esz[3] = {8, 4, 2};
@@ -399,6 +416,15 @@ dwf_status launch_pack_gauge(dwf_lattice* L, const void* U) {
   pack_gauge_kernel<__half><<<blocks, 256, 0, L->stream>>>(u, geo(L), L->p.bc_t, (__half*)L->links[2][0], (__half*)L->links[2][1]);
   counted(L, 2);
   DWF_LAUNCHED(L);
+  for (int par = 0; par < 2; ++par) {
+    if (!L->links_dm[par]) {
+      cudaError_t e = cudaMalloc(&L->links_dm[par], (size_t)L->Vh * 8 * 20 * sizeof(float));
+      if (e != cudaSuccess) return cuda_check(L, e, "gauge copy (direction-major)");
+    }
+    links_direction_major<<<(unsigned)((L->Vh * 8 + 255) / 256), 256, 0, L->stream>>>(
+        (const float*)L->links[1][par], L->links_dm[par], L->Vh);
+    DWF_LAUNCHED(L);
+  }
   return DWF_OK;
 }
 
@@ -576,6 +602,7 @@ dwf_status dwf_destroy_lattice(dwf_lattice_t L) {
   for (int i = 0; i < 2; ++i) cudaFree(L->nbr[i]);
   for (int p = 0; p < 3; ++p)
     for (int i = 0; i < 2; ++i) cudaFree(L->links[p][i]);
+  for (int i = 0; i < 2; ++i) cudaFree(L->links_dm[i]);
   for (auto& o : L->sops) {
     cudaFree(o.d64);
     cudaFree(o.d32);
@@ -613,6 +640,12 @@ dwf_status dwf_get_kernel_time(dwf_lattice_t L, dwf_prec prec, double* ms, long 
   if (ms) *ms = L->t_ms[prec];
   if (launches) *launches = L->t_n[prec];
   if (bytes) *bytes = L->t_bytes[prec];
+  return DWF_OK;
+}
+
+dwf_status dwf_set_wait_limit(dwf_lattice_t L, long long polls) {
+  if (!L) return fail(L, DWF_ERR_INVALID_ARG, "dwf_set_wait_limit: null handle");
+  L->wait_limit = polls < 0 ? kHopWaitLimit : (long)polls;
   return DWF_OK;
 }
 

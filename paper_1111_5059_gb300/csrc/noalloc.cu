@@ -4,13 +4,12 @@
 // dwf_apply_Mpc takes its packed FP64 fields from the handle's workspace,
 // which the library allocates with cudaMalloc on first use (and its
 // fifth-dimension coefficient tables with cudaMalloc on the first call with
-// a new mass).  Code that must not allocate while it runs -- work captured
-// into a CUDA graph, code under an allocator that owns all device memory, or
-// a real-time loop that may not stall on the driver -- calls this entry
-// point instead.  Its scratch is one file-scope device array of fixed size,
-// present on every GPU that loads the library until the process exits; the
-// fifth-dimension operators are passed to the kernels as by-value
-// coefficients, so no table is allocated either.
+// a new mass).  Code that must not allocate while it runs -- code under an
+// allocator that owns all device memory, or a loop that may not stall on the
+// driver -- calls this entry point instead.  Its scratch is one file-scope
+// device array of fixed size, present on every GPU that loads the library
+// until the process exits; the fifth-dimension operators are passed to the
+// kernels as by-value coefficients, so no table is allocated either.
 #include <cmath>
 #include <mutex>
 
@@ -41,40 +40,6 @@ dwf_status scratch_address(dwf_lattice* L, void** out) {
   return DWF_OK;
 }
 
-// Structured fifth-dimension descriptors for mass m, computed on the host
-// (the same operators as the library's tables: A = (4-M5)(b+cQ) + 1 - Q,
-// B = b + cQ, E1 = B A^-1, E0 = A B^-1).  Returns false if one of them would
-// need the dense fallback, which this entry point does not provide.
-bool host_descriptors(const dwf_lattice* L, double m, SOps* o) {
-  const double b = L->p.b, c = L->p.c, w = 4.0 - L->p.M5;
-  const double al = w * b + 1.0, be = w * c - 1.0;
-  const double f[SOps::NKIND][4] = {
-      {al, be, 1, 0}, {al, be, 1, 0}, {1, 0, al, be}, {1, 0, al, be}, {b, c, 1, 0},   {b, c, 1, 0},
-      {1, 0, b, c},   {1, 0, b, c},   {b, c, al, be}, {b, c, al, be}, {al, be, b, c}, {al, be, b, c},
-  };
-  o->m = m;
-  for (int k = 0; k < SOps::NKIND; ++k) {
-    SOpDesc& d = o->desc[k];
-    const double g1 = f[k][0], d1 = f[k][1], g2 = f[k][2], d2 = f[k][3];
-    if (g2 == 0.0) return false;
-    d.trans = k & 1;
-    d.dense_kind = k;
-    d.g1 = g1;
-    d.d1 = d1;
-    d.m = m;
-    d.has_inv = d2 != 0.0;
-    d.ginv = 1.0 / g2;
-    d.rho = -d2 / g2;
-    const double den = 1.0 + m * std::pow(d.rho, L->Ls);
-    d.c0 = 1.0 / (g2 * den);
-    const bool identity = g1 == 1.0 && d1 == 0.0 && g2 == 1.0 && d2 == 0.0;
-    const bool stable = !d.has_inv || (std::fabs(d.rho) <= 1.0 && std::fabs(den) > 1e-8);
-    if (!stable) return false;
-    d.kind = identity ? 0 : 1;
-  }
-  return true;
-}
-
 }  // namespace
 
 }  // namespace dwf
@@ -92,9 +57,12 @@ extern "C" dwf_status dwf_apply_Mpc_noalloc(dwf_lattice_t L, double m, int dag, 
                 "dwf_apply_Mpc_noalloc: lattice too large for the fixed scratch (needs " + std::to_string(4 * fb) +
                     " bytes, DWF_NOALLOC_SCRATCH_BYTES = " + std::to_string((size_t)DWF_NOALLOC_SCRATCH_BYTES) + ")");
   SOps ops{};
-  if (!host_descriptors(L, m, &ops))
-    return fail(L, DWF_ERR_INVALID_ARG,
-                "dwf_apply_Mpc_noalloc: these Moebius parameters need the dense fifth-dimension fallback");
+  ops.m = m;
+  fifth_descriptors(L->p, L->Ls, m, ops.desc);
+  for (int k = 0; k < SOps::NKIND; ++k)
+    if (ops.desc[k].kind == 2)
+      return fail(L, DWF_ERR_INVALID_ARG,
+                  "dwf_apply_Mpc_noalloc: these Moebius parameters need the dense fifth-dimension fallback");
   void* base = nullptr;
   DWF_TRY(scratch_address(L, &base));
   unsigned char* p = reinterpret_cast<unsigned char*>(base);
@@ -106,7 +74,9 @@ extern "C" dwf_status dwf_apply_Mpc_noalloc(dwf_lattice_t L, double m, int dag, 
   t.v = p + 2 * fb;
   u.v = p + 3 * fb;
   // every word the kernels read is written earlier in this call, so nothing
-  // needs clearing; kernel timing (event creation) is suspended for the call
+  // needs clearing: the FP64 per-slice kernels (pack, s-local, hop) read and
+  // write only the slices s < Ls, never the padding slot of an odd Ls.  Kernel
+  // timing (event creation) is suspended for the call.
   const bool timing = L->timing;
   L->timing = false;
   dwf_status st = launch_pack(L, in, 0, xe);

@@ -120,6 +120,8 @@ def _declare(lib):
         "dwf_get_kernel_time": [H, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                 ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)],
         "dwf_get_launch_count": [H, ctypes.POINTER(ctypes.c_longlong)],
+        "dwf_apply_Mpc_prec": [H, ctypes.c_double, ctypes.c_int, ctypes.c_int, _VP, _VP],
+        "dwf_set_wait_limit": [H, ctypes.c_longlong],
     }
     for name, args in sigs.items():
         fn = getattr(lib, name)
@@ -249,21 +251,44 @@ class Lattice:
                    _VP(_ptr(out, self.spinor_shape)))
         return out
 
+    def apply_Mpc_prec(self, m: float, x: torch.Tensor, prec: str = "f32", dag: bool = False,
+                       out=None) -> torch.Tensor:
+        """M_pc (or M_pc^+) evaluated with fields stored at `prec` ("f64", "f32",
+        "f16") through the launches the solvers' inner iterations use (see
+        include/dwf.h, dwf_apply_Mpc_prec)."""
+        out = self._new() if out is None else out
+        self._call(lib().dwf_apply_Mpc_prec, float(m), int(bool(dag)), _PREC[prec], _VP(_ptr(x, self.spinor_shape)),
+                   _VP(_ptr(out, self.spinor_shape)))
+        return out
+
+    def set_wait_limit(self, polls: int = -1):
+        """Polls of the hop kernel's bounded consumer waits on later launches
+        (-1: the default; 0: every wait gives up at once)."""
+        self._call(lib().dwf_set_wait_limit, int(polls))
+
     def apply_Mpc_noalloc(self, m: float, x: torch.Tensor, out: torch.Tensor, dag: bool = False) -> torch.Tensor:
         """apply_Mpc into a caller-provided `out`; the library allocates no
-        device memory during the call (for callers that must not allocate,
-        e.g. while recording a CUDA graph; see include/dwf.h)."""
+        device memory during the call (for callers whose allocator owns the
+        device memory or that may not stall on the driver; see include/dwf.h)."""
         self._call(lib().dwf_apply_Mpc_noalloc, float(m), int(bool(dag)), _VP(_ptr(x, self.spinor_shape)),
                    _VP(_ptr(out, self.spinor_shape)))
         return out
 
     def cg(self, m: float, b: torch.Tensor, x0=None, tol=1e-10, max_iter=100000, inner="f64",
-           delta=0.1, check_every=10, raise_on_fail=True) -> SolveResult:
+           delta=0.1, check_every=10, raise_on_fail=True, out=None) -> SolveResult:
         """Solve D(m) x = b (Sec. 4, Eq. dirac_eq) by even-odd CG on the normal
         equations to |b - D(m) x| / |b| <= tol: plain FP64 (inner="f64") or mixed
         precision with FP32 / FP16-stored inner iterations and FP64 reliable
-        updates (delta).  x0 is the initial guess (zeros if None)."""
-        x = torch.zeros_like(b) if x0 is None else x0.clone()
+        updates (delta).  x0 is the initial guess (zeros if None).  `out`, if
+        given, receives the solution (it is overwritten by the guess first)."""
+        if out is None:
+            x = torch.zeros_like(b) if x0 is None else x0.clone()
+        else:
+            x = out
+            if x0 is None:
+                x.zero_()
+            else:
+                x.copy_(x0)
         prm = CGParams(float(tol), int(max_iter), _PREC[inner], float(delta), int(check_every))
         st = Stats()
         with torch.cuda.device(self.device):
@@ -297,10 +322,11 @@ class Lattice:
 
 def madwf_solve(outer: Lattice, inner: Lattice, m: float, b: torch.Tensor, n_dc=3, tol_pv=1e-8, tol_mob=1e-5,
                 tol_final=1e-10, inner_prec="f32", max_iter=100000, delta=0.1, check_every=10,
-                raise_on_fail=True) -> SolveResult:
+                raise_on_fail=True, out=None) -> SolveResult:
     """Moebius-accelerated solve of D_DW(m) x = b on `outer` through the Moebius
-    lattice `inner` (see include/dwf.h, madwf_solve)."""
-    x = torch.empty_like(b)
+    lattice `inner` (see include/dwf.h, madwf_solve); `out`, if given,
+    receives the solution."""
+    x = torch.empty_like(b) if out is None else out
     prm = MadwfParams(int(n_dc), float(tol_pv), float(tol_mob), float(tol_final), _PREC[inner_prec],
                       int(max_iter), float(delta), int(check_every))
     st = MadwfStats()

@@ -145,6 +145,8 @@ def test_null_handle_is_rejected_by_every_entry_point(lib):
         ("dwf_set_kernel_timing", lambda: L.dwf_set_kernel_timing(None, 1), "dwf_set_kernel_timing:"),
         ("dwf_get_kernel_time", lambda: L.dwf_get_kernel_time(None, 0, None, None, None), "dwf_get_kernel_time:"),
         ("dwf_get_launch_count", lambda: L.dwf_get_launch_count(None, None), "dwf_get_launch_count:"),
+        ("dwf_apply_Mpc_prec", lambda: L.dwf_apply_Mpc_prec(None, 0.1, 0, 1, None, None), "dwf_apply_Mpc_prec:"),
+        ("dwf_set_wait_limit", lambda: L.dwf_set_wait_limit(None, 0), "dwf_set_wait_limit:"),
     ]
     for name, call, prefix in calls:
         assert call() == 1, name

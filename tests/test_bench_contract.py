@@ -27,7 +27,11 @@ def test_reference_arm_json_line():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["unit"] == "s"
     assert isinstance(cb["cores"], int) and 1 <= cb["cores"] <= (os.cpu_count() or 1)
-    assert "t-slab" in cb["sample"]
+    assert "sub-lattice" in cb["sample"] and cb["cores"] >= 1
+    # the measured step and its extrapolation are reported apart
+    ex = d["extrapolated"]
+    assert abs(ex["step_seconds"] * 1e3 - d["ms_per_step"]) < 1e-6 * d["ms_per_step"]
+    assert ex["volume_factor"] > 0 and ex["iterations"] > 0
     # rates of the oracle: four hops per CG iteration over the 16^3 x 32 x 16 half lattice
     assert cb["hops_per_s"] > 0 and cb["algorithmic_gbs"] > 0
     sites = 16 * 16 * 16 * 32 // 2 * 16

@@ -11,9 +11,10 @@
   * One FGI PQPQP step equals the oracle's step; it is reversible (p -> -p)
     to solver precision, and force-gradient forecasting (Sec. 2) reduces the
     iterations of the second solve.
-  * At 16^3 x 8 x Ls=16 (the force workload's size): finite differences of
-    the GPU action along a random direction against the force, and
-    reversibility of one step.
+  * At 16^3 x 8 x Ls=16 (the force workload's size): the GPU's solutions X
+    by the oracle's operator, S and F against the oracle's formulas on those
+    X to 1e-9; finite differences of the GPU action along a random direction
+    against the force, and reversibility of one step.
 """
 import numpy as np
 import pytest
@@ -116,6 +117,40 @@ def test_fgi_step_matches_oracle_and_is_reversible(small, dwf):
     assert np.abs(Ut.cpu().numpy() - U).max() < 1e-10
     assert np.abs(-pt.cpu().numpy() - p).max() < 1e-9
     lat.set_gauge(_to(U))
+
+
+def test_force_workload_size_matches_oracle(dwf):
+    """16^3 x 8 x Ls=16 with quotient terms (0.01, 0.1) and (0.1, 1.0): the
+    GPU's solutions X are checked by the oracle's operator (|M2^+ phi -
+    M1^+ M1 X| <= 1e-12 |M2^+ phi|, the solve's target), and the GPU's S and F against the
+    oracle's action and force evaluated on those same X (Sec. 2: F^j = e_j S),
+    F to 1e-9 relative to its largest component.  The residual bar allows
+    1.5x the solve's target for the rounding of M1^+ M1 X in FP64, which the
+    library's and the oracle's evaluations do in different orders."""
+    dims, Ls = (16, 16, 16, 8), 16
+    terms = [(0.01, 0.1), (0.1, 1.0)]
+    U = I.gauge_field(4, dims, 0.5)
+    lat = dwf.Lattice(dims, Ls, M5)
+    lat.set_gauge(_to(U))
+    eta = [I.gaussian_spinor(50 + k, dims, Ls) for k in range(2)]
+    phit = [_to(e) for e in eta]
+    Xs = [torch.zeros_like(p) for p in phit]
+    S, F, _, _ = dwf.force(lat, terms, phit, X_io=Xs, tol=1e-12)
+    lat.close()
+    Fo = np.zeros(F.shape)
+    So = 0.0
+    for (m1, m2), phi, Xt in zip(terms, eta, Xs):
+        X = Xt.cpu().numpy()
+        eo1, eo2 = O.EO(U, m1, M5, Ls), O.EO(U, m2, M5, Ls)
+        v = eo2.Mpc(phi * eo2.even, True)
+        Y = eo1.Mpc(X)
+        res = np.sqrt(O.norm2(v - eo1.Mpc(Y, True)) / O.norm2(v))
+        assert res <= 1.5e-12, (m1, m2, res)
+        So += O.norm2(Y)
+        Fo += O.quotient_force(U, X, Y, phi * eo2.even, m1, m2, M5)
+    assert abs(S - So) <= 1e-11 * So
+    Fg = F.cpu().numpy()
+    assert np.abs(Fg - Fo).max() <= 1e-9 * np.abs(Fo).max()
 
 
 def test_force_workload_size_properties(dwf):

@@ -1,20 +1,27 @@
-"""Solves at the benchmark sizes, checked on sampled sites by the oracle.
+"""Solves at the benchmark sizes, checked by the ORACLE's operator.
 
-The oracle evaluates (D(m) x)(s, n) one 5D site at a time from its
-definition; at every sampled site the residual b - D x must not exceed the
-global bound tol * |b| that the solve claims (a single entry is bounded by
-the norm).  Sizes and parameters are those bench.py times:
-
-  * Shamir 16^3 x 32 x Ls=16, m_f = 0.01, eps = 0.5, seed 2: FP64 CG to
-    1e-12 and mixed FP32 / FP16-storage CG to 1e-10;
-  * MADWF: Shamir 24^3 x 64 x Ls=32, m_f = 0.002, eps = 0.6, seed 3, through
-    Moebius Ls'=12 (b = 11/6, c = 5/6), three defect-correction passes,
-    Pauli-Villars tolerance 1e-6, Moebius 1e-5, final 1e-10.
+The primary criterion is the one the solve claims (Sec. 4: D_DW(m) x = b to a
+relative residual): |b - D(m) x| / |b| of the GPU's x, computed by the FP64
+oracle,
+  * over the whole lattice at 16^3 x 32 x Ls=16 (m_f = 0.01, eps = 0.5,
+    seed 2): FP64 CG to 1e-12, mixed FP32 / FP16-storage CG to 1e-10;
+  * over the whole lattice at 16^3 x 8 x Ls=16 (the force workload's
+    lattice, m = 0.01, eps = 0.5, seed 4): FP64 CG to 1e-12, mixed FP32 CG
+    to 1e-10;
+  * at 24^3 x 64 x Ls=32 (the MADWF workload: m_f = 0.002, eps = 0.6, seed 3,
+    through Moebius Ls' = 12 with b = 11/6, c = 5/6, three defect-correction
+    passes, Pauli-Villars tolerance 1e-6, Moebius 1e-5, final 1e-10), where a
+    whole-lattice oracle pass does not fit the test's time, on two slabs of
+    four timeslices (one across the periodic t boundary), 8 of the 64: the
+    residual norm over them must be <= 1e-10 |b| (a necessary condition of
+    the claimed total, and, the residual being spread over the lattice, the
+    slabs' share of it is about sqrt(8/64) of the total).
 """
 import numpy as np
 import pytest
 import torch
 
+import oracle_residual as R
 from oracle import dwf_oracle as O
 from paper_1111_5059_gb300 import inputs as I
 
@@ -23,21 +30,9 @@ pytestmark = pytest.mark.gpu
 M5 = 1.8
 
 
-def _sites(dims, Ls, n, seed):
-    rng = np.random.default_rng(seed)
-    X, Y, Z, T = dims
-    pick = [(0, 0, 0, 0, 0), (Ls - 1, T - 1, Z - 1, Y - 1, X - 1)]  # both walls, both corners
-    pick += [tuple(int(v) for v in (rng.integers(Ls), rng.integers(T), rng.integers(Z), rng.integers(Y),
-                                    rng.integers(X))) for _ in range(n)]
-    return pick
-
-
-def _check_sampled(U, x, b, m, tol, sites, b5=1.0, c5=0.0):
-    got = O.dwf_op_at(U, x, m, M5, b5, c5, 1, sites)
-    want = np.array([b[s] for s in sites])
-    bound = tol * np.sqrt(O.norm2(b))
-    worst = float(np.abs(got - want).max())
-    assert worst <= bound, (worst, bound)
+def _oracle_resid(U, x, b, m, b5=1.0, c5=0.0):
+    r = b - O.dwf_op(U, x, m, M5, b5, c5, 1)
+    return np.sqrt(O.norm2(r) / O.norm2(b))
 
 
 @pytest.fixture(scope="module")
@@ -47,20 +42,38 @@ def mixed_case(dwf):
     b = I.gaussian_spinor(2, dims, Ls)
     lat = dwf.Lattice(dims, Ls, M5)
     lat.set_gauge(torch.from_numpy(U).cuda())
-    yield lat, U, b, _sites(dims, Ls, 30, 11)
+    yield lat, U, b
     lat.close()
 
 
 @pytest.mark.parametrize("inner,tol", [("f64", 1e-12), ("f32", 1e-10), ("f16", 1e-10)])
-def test_cg_16x32_Ls16_sampled(mixed_case, inner, tol):
-    lat, U, b, sites = mixed_case
+def test_cg_16x32_Ls16_whole_lattice_oracle_residual(mixed_case, inner, tol):
+    lat, U, b = mixed_case
     r = lat.cg(0.01, torch.from_numpy(b).cuda(), tol=tol, inner=inner, delta=0.01)
     assert r.stats["true_resid"] <= tol
-    _check_sampled(U, r.x.cpu().numpy(), b, 0.01, tol, sites)
+    res = _oracle_resid(U, r.x.cpu().numpy(), b, 0.01)
+    assert res <= tol, res
+    # the library's own FP64 residual agrees with the oracle's (up to the
+    # rounding of b - D x in FP64, ~1e-15 relative here)
+    assert abs(res - r.stats["true_resid"]) <= 0.01 * res + 1e-14
 
 
-def test_madwf_24x64_Ls32_sampled(dwf):
+@pytest.mark.parametrize("inner,tol", [("f64", 1e-12), ("f32", 1e-10)])
+def test_cg_16x8_Ls16_whole_lattice_oracle_residual(dwf, inner, tol):
+    dims, Ls, m = (16, 16, 16, 8), 16, 0.01
+    U = I.gauge_field(4, dims, 0.5)
+    b = I.gaussian_spinor(4, dims, Ls)
+    lat = dwf.Lattice(dims, Ls, M5)
+    lat.set_gauge(torch.from_numpy(U).cuda())
+    r = lat.cg(m, torch.from_numpy(b).cuda(), tol=tol, inner=inner, delta=0.01)
+    res = _oracle_resid(U, r.x.cpu().numpy(), b, m)
+    assert res <= tol, res
+    lat.close()
+
+
+def test_madwf_24x64_Ls32_slab_oracle_residual(dwf):
     dims, Ls, Lp = (24, 24, 24, 64), 32, 12
+    T = dims[3]
     U = I.gauge_field(3, dims, 0.6)
     b = I.gaussian_spinor(3, dims, Ls)
     Ut = torch.from_numpy(U).cuda()
@@ -75,6 +88,17 @@ def test_madwf_24x64_Ls32_sampled(dwf):
     # the defect correction reduces the residual pass by pass (Sec. 5)
     pr = st["pass_resid"]
     assert all(pr[k + 1] < pr[k] for k in range(len(pr) - 1))
-    _check_sampled(U, r.x.cpu().numpy(), b, 0.002, 1e-10, _sites(dims, Ls, 30, 12))
     outer.close()
     inner.close()
+    r2 = 0.0
+    for t0 in (T - 2, T // 2):  # the first slab crosses the periodic t boundary
+        rows = R.slab_rows(T, t0, 4)
+        xs = r.x[:, rows].cpu().numpy()
+        rr, _ = R.slab_residual(U, xs, b[:, rows[1:-1]], rows, 0.002, M5)
+        r2 += rr
+    rel = np.sqrt(r2 / O.norm2(b))
+    assert rel <= 1e-10, rel
+    # the slabs hold 8 of 64 timeslices: with the residual spread over the
+    # lattice their share of the library's reported total is ~sqrt(8/64); a
+    # total under-reported by a large factor would fail this
+    assert rel <= 4 * np.sqrt(8 / 64) * st["total"]["true_resid"] + 1e-14, (rel, st["total"]["true_resid"])

@@ -1,8 +1,10 @@
 """The allocation-free entry point dwf_apply_Mpc_noalloc, for callers that
-must not allocate device memory while they run (work recorded into a CUDA
-graph, code whose allocator owns all device memory): it must give the same
-result as dwf_apply_Mpc, on repeated calls that reuse its fixed scratch, and
-refuse lattices larger than that scratch.
+must not allocate device memory while they run (code whose allocator owns
+all device memory, loops that may not stall on the driver): it must give the
+same result as dwf_apply_Mpc, on repeated calls that reuse its fixed
+scratch (an odd Ls included, whose padding slot the scratch never clears),
+leave the device's free memory unchanged on a fresh handle, and refuse
+lattices larger than that scratch.
 
 This file is collected last on purpose, so that a run stopping at the first
 failure has already run every other test.
@@ -27,7 +29,8 @@ def _rel(a, b):
 
 
 @pytest.mark.parametrize("case", [((4, 4, 4, 4), 8, 1.0, 0.0, 1, 0.04), ((4, 2, 4, 6), 12, 1.5, 0.5, -1, 0.01),
-                                  ((8, 8, 8, 8), 16, 11 / 6, 5 / 6, 1, 0.002)])
+                                  ((8, 8, 8, 8), 16, 11 / 6, 5 / 6, 1, 0.002),
+                                  ((2, 4, 2, 4), 5, 11 / 6, 5 / 6, -1, 0.3)])
 def test_noalloc_matches_apply_Mpc_on_repeated_calls(dwf, case):
     dims, Ls, b, c, bc_t, m = case
     lat = dwf.Lattice(dims, Ls, M5, b, c, bc_t)
@@ -40,6 +43,29 @@ def test_noalloc_matches_apply_Mpc_on_repeated_calls(dwf, case):
             got = lat.apply_Mpc_noalloc(m, x, out, dag=dag)
             assert got.data_ptr() == out.data_ptr()
             assert _rel(got, want) < 1e-13
+    lat.close()
+
+
+def test_noalloc_leaves_free_device_memory_unchanged(dwf):
+    dims, Ls, m = (8, 8, 8, 8), 16, 0.01
+    U = _to(I.gauge_field(9, dims, 0.5))
+    x = _to(I.gaussian_spinor(3, dims, Ls))
+    out = torch.empty_like(x)
+    # load every kernel module the call uses (lazy module loading allocates
+    # device memory on a module's first use, outside this entry point's control)
+    warm = dwf.Lattice(dims, Ls, M5)
+    warm.set_gauge(U)
+    warm.apply_Mpc_noalloc(m, x, out)
+    warm.close()
+    lat = dwf.Lattice(dims, Ls, M5)
+    lat.set_gauge(U)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for dag in (False, True):
+        lat.apply_Mpc_noalloc(m, x, out, dag=dag)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
     lat.close()
 
 

@@ -246,6 +246,27 @@ dwf_status dwf_kinetic(dwf_lattice_t h, const void* p, double* T);
 dwf_status fgi_step(dwf_lattice_t h, int nterms, const dwf_quotient* terms, const void* const* phi, void* U, void* p,
                     double tau, int forecast, const dwf_cg_params* cg, dwf_stats* stats, int* fg_iters);
 
+/* A molecular-dynamics trajectory of nsteps steps of length tau (Sec. 2):
+ * DWF_INTEGRATOR_FGI, the force-gradient step of fgi_step,
+ *   P(tau/6) Q(tau/2) [F(U); U' = exp(-tau^2/24 F^j T_j) U; p -= 2/3 tau F(U')] Q(tau/2) P(tau/6),
+ * or DWF_INTEGRATOR_OMELYAN, the second-order minimum-norm step the paper
+ * compares it with (Omelyan, Mryglod and Folk 2003, lambda = 0.1931833275037836),
+ *   P(lambda tau) Q(tau/2) P((1 - 2 lambda) tau) Q(tau/2) P(lambda tau).
+ * The closing momentum update of a step and the opening one of the next act
+ * at the same U and are applied as one, so a trajectory evaluates the force
+ * 3 nsteps + 1 (FGI) or 2 nsteps + 1 (Omelyan) times.  With forecast != 0 the
+ * FGI solve at U' starts from the solutions at U (Sec. 2).  U (device
+ * complex128 boundary layout) and p (device float64 [4][T][Z][Y][X][8]) are
+ * updated in place and the handle's gauge field is left set to the final U.
+ * H0 and H1 (may be NULL) receive H = 1/2 sum (p^j)^2 + S at the start and the
+ * end in FP64; S comes from the first and the last force evaluation, so they
+ * cost no extra solve.  stats (may be NULL) sums the solves; nforce (may be
+ * NULL) receives the number of force evaluations. */
+typedef enum { DWF_INTEGRATOR_FGI = 0, DWF_INTEGRATOR_OMELYAN = 1 } dwf_integrator;
+dwf_status dwf_md_trajectory(dwf_lattice_t h, int nterms, const dwf_quotient* terms, const void* const* phi, void* U,
+                             void* p, double tau, int nsteps, dwf_integrator integ, int forecast,
+                             const dwf_cg_params* cg, double* H0, double* H1, dwf_stats* stats, int* nforce);
+
 /* dwf_apply_Mpc without any device allocation (the paper has no counterpart;
  * this serves callers that must not allocate while they run: code whose
  * allocator owns all device memory, loops that may not stall on the driver).  Same operator, arguments and boundary

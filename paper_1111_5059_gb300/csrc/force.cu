@@ -558,6 +558,78 @@ dwf_status fgi_step(dwf_lattice_t L, int nterms, const dwf_quotient* terms, cons
   return DWF_OK;
 }
 
+// Omelyan, Mryglod and Folk, Comput. Phys. Commun. 151 (2003) 272: the
+// second-order minimum-norm ("2MN") parameter of the integrator that Sec. 2
+// compares the force-gradient integrator with.
+static constexpr double kOmelyanLambda = 0.1931833275037836;
+
+dwf_status dwf_md_trajectory(dwf_lattice_t L, int nterms, const dwf_quotient* terms, const void* const* phi, void* U,
+                             void* p, double tau, int nsteps, dwf_integrator integ, int forecast,
+                             const dwf_cg_params* cg, double* H0, double* H1, dwf_stats* stats, int* nforce) {
+  if (!L || nterms < 1 || nterms > 64 || !terms || !phi || !U || !p || !cg || !std::isfinite(tau) || nsteps < 1 ||
+      (integ != DWF_INTEGRATOR_FGI && integ != DWF_INTEGRATOR_OMELYAN))
+    return fail(L, DWF_ERR_INVALID_ARG, "dwf_md_trajectory: bad argument");
+  auto t0 = std::chrono::steady_clock::now();
+  const long long l0 = L->launches;
+  const long V4 = L->V4;
+  const size_t fbytes = (size_t)4 * V4 * 8 * sizeof(double);
+  const size_t ubytes = (size_t)4 * V4 * 18 * sizeof(double);
+  const size_t sbytes = (size_t)2 * L->Vh * L->Ls * 24 * sizeof(double);
+  void *F, *Up, *xbuf;
+  DWF_TRY(ws_get(L, "fgi.F", fbytes, &F));
+  DWF_TRY(ws_get(L, "fgi.Up", ubytes, &Up));
+  DWF_TRY(ws_get(L, "fgi.X", sbytes * nterms, &xbuf));
+  std::vector<void*> X(nterms);
+  for (int t = 0; t < nterms; ++t) X[t] = reinterpret_cast<char*>(xbuf) + t * sbytes;
+  dwf_stats tot{};
+  int count = 0;
+  // F (and the action S) at Ucur; keep: store the solutions; guess: start from them
+  auto force = [&](const void* Ucur, bool keep, bool guess, double* S) -> dwf_status {
+    DWF_TRY(dwf_set_gauge(L, Ucur));
+    if (!guess) DWF_CUDA(L, cudaMemsetAsync(xbuf, 0, sbytes * nterms, L->stream));
+    dwf_stats s{};
+    DWF_TRY(dwf_force(L, nterms, terms, phi, (keep || guess) ? X.data() : nullptr, F, nullptr, S, cg, &s));
+    add_stats(&tot, s);
+    ++count;
+    return DWF_OK;
+  };
+  const bool fgi = integ == DWF_INTEGRATOR_FGI;
+  const double a = fgi ? 1.0 / 6.0 : kOmelyanLambda;  // weight of the end momentum updates
+  double S = 0.0, T = 0.0;
+  DWF_TRY(force(U, false, false, &S));
+  if (H0) {
+    DWF_TRY(dwf_kinetic(L, p, &T));
+    *H0 = T + S;
+  }
+  DWF_TRY(dwf_momentum_update(L, F, -a * tau, p));
+  for (int k = 0; k < nsteps; ++k) {
+    DWF_TRY(fgi_link_update(L, p, tau / 2.0, U, U));
+    if (fgi) {
+      // force-gradient step: F(U); U' = exp(-tau^2/24 F) U; p -= 2/3 tau F(U')
+      DWF_TRY(force(U, forecast != 0, false, nullptr));
+      DWF_TRY(fgi_link_update(L, F, -tau * tau / 24.0, U, Up));
+      DWF_TRY(force(Up, false, forecast != 0, nullptr));
+      DWF_TRY(dwf_momentum_update(L, F, -2.0 * tau / 3.0, p));
+    } else {
+      DWF_TRY(force(U, false, false, nullptr));
+      DWF_TRY(dwf_momentum_update(L, F, -(1.0 - 2.0 * a) * tau, p));
+    }
+    DWF_TRY(fgi_link_update(L, p, tau / 2.0, U, U));
+    // the closing update of this step and the opening one of the next act at the same U
+    DWF_TRY(force(U, false, false, &S));
+    DWF_TRY(dwf_momentum_update(L, F, -(k == nsteps - 1 ? a : 2.0 * a) * tau, p));
+  }
+  if (H1) {
+    DWF_TRY(dwf_kinetic(L, p, &T));
+    *H1 = T + S;
+  }
+  tot.launches = L->launches - l0;
+  tot.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (stats) *stats = tot;
+  if (nforce) *nforce = count;
+  return DWF_OK;
+}
+
 dwf_status dwf_kinetic(dwf_lattice_t L, const void* p, double* T) {
   if (!L || !p || !T) return fail(L, DWF_ERR_INVALID_ARG, "dwf_kinetic: bad argument");
   const long n = 4 * L->V4 * 8;

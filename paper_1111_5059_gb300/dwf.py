@@ -122,6 +122,10 @@ def _declare(lib):
         "dwf_get_launch_count": [H, ctypes.POINTER(ctypes.c_longlong)],
         "dwf_apply_Mpc_prec": [H, ctypes.c_double, ctypes.c_int, ctypes.c_int, _VP, _VP],
         "dwf_set_wait_limit": [H, ctypes.c_longlong],
+        "dwf_md_trajectory": [H, ctypes.c_int, ctypes.POINTER(Quotient), ctypes.POINTER(_VP), _VP, _VP,
+                              ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(CGParams),
+                              ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                              ctypes.POINTER(Stats), ctypes.POINTER(ctypes.c_int)],
     }
     for name, args in sigs.items():
         fn = getattr(lib, name)
@@ -409,6 +413,24 @@ def fgi_step(lat: Lattice, terms, phis, U: torch.Tensor, p: torch.Tensor, tau: f
               _VP(_ptr(U, lat.gauge_shape)), _VP(_ptr(p, dtype=torch.float64)), float(tau), int(bool(forecast)),
               ctypes.byref(prm), ctypes.byref(st), fg)
     return st.as_dict(), (fg[0], fg[1])
+
+
+INTEGRATORS = {"fgi": 0, "omelyan": 1}
+
+
+def md_trajectory(lat: Lattice, terms, phis, U: torch.Tensor, p: torch.Tensor, tau: float, nsteps: int,
+                  integrator="fgi", forecast=True, tol=1e-12, inner="f64", max_iter=100000, delta=0.1):
+    """A molecular-dynamics trajectory (see include/dwf.h, dwf_md_trajectory); U and p
+    are updated in place.  Returns (H0, H1, stats, force evaluations)."""
+    H0, H1 = ctypes.c_double(), ctypes.c_double()
+    st = Stats()
+    nf = ctypes.c_int()
+    prm = CGParams(float(tol), int(max_iter), _PREC[inner], float(delta), 10)
+    lat._call(lib().dwf_md_trajectory, len(terms), _terms(terms), _ptr_array(phis, lat.spinor_shape),
+              _VP(_ptr(U, lat.gauge_shape)), _VP(_ptr(p, dtype=torch.float64)), float(tau), int(nsteps),
+              INTEGRATORS[integrator], int(bool(forecast)), ctypes.byref(prm), ctypes.byref(H0), ctypes.byref(H1),
+              ctypes.byref(st), ctypes.byref(nf))
+    return H0.value, H1.value, st.as_dict(), nf.value
 
 
 def hamiltonian(lat: Lattice, terms, phis, U: torch.Tensor, p: torch.Tensor, tol=1e-12) -> float:

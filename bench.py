@@ -16,11 +16,14 @@ A step is one solve from a zero guess on seeded synthetic inputs already
 resident in HBM (timed with CUDA events on the solve's stream).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload madwf|mixed|hopprof|ladder]
-                  [--impl native|reference] [--study] [--no-fp64] [--no-extras] [--no-cpu-baseline]
+                  [--impl native|reference] [--study] [--md-study] [--no-fp64] [--no-extras]
+                  [--no-cpu-baseline]
 
 --study (with the madwf workload) sweeps the MADWF settings (defect-correction
-passes, Pauli-Villars and Moebius tolerances, the Moebius scale b + c) and
-prints one JSON line per setting.
+passes, Pauli-Villars and Moebius tolerances, the Moebius scale b + c, and two
+rougher gauge fields) and prints one JSON line per setting; --md-study prints
+force-gradient against Omelyan trajectories (dH, force evaluations, time) at
+several step sizes on the 16^3 x 8 x Ls=16 force workload.
 
 Under torchrun (N > 1) every rank solves its own replica (no collective on
 the data path, "replicas only"); rank 0 prints the JSON line with the max
@@ -55,16 +58,22 @@ HOP_TRAFFIC = {"source_sha256_prefix": "dc5de73caaafee4b", "ratio": 1.105}
 
 WORKLOADS = {
     # MADWF: Shamir 24^3 x 64 x Ls=32, m_f = 0.002, eps = 0.6, through Moebius Ls' = 12 with
-    # b - c = 1 and b + c = Ls / Ls' (b = 11/6, c = 5/6); 3 defect-correction passes.
+    # b - c = 1 and b + c = Ls / Ls' (b = 11/6, c = 5/6).  Defect-correction passes and the
+    # intermediate tolerances are the fastest setting of the --study sweep on this input (one
+    # pass, Pauli-Villars 1e-3, Moebius 1e-2; three passes at 1e-6 / 1e-5 took 2.5x longer).
     "madwf": dict(name="madwf-shamir-24^3x64-Ls32-via-mobius-Ls12", dims=(24, 24, 24, 64), Ls=32, M5=1.8,
-                  m=0.002, eps=0.6, seed=3, inner="f32", madwf=True, inner_Ls=12, b=11 / 6, c=5 / 6, n_dc=3,
-                  tol_pv=1e-6, tol_mob=1e-5, sample=(24, 24, 4, 2)),
+                  m=0.002, eps=0.6, seed=3, inner="f32", madwf=True, inner_Ls=12, b=11 / 6, c=5 / 6, n_dc=1,
+                  tol_pv=1e-3, tol_mob=1e-2, sample=(24, 24, 4, 2)),
     # 16^3 x 32 x Ls=16 Shamir, m_f = 0.01, eps = 0.5: mixed-precision CG
     "mixed": dict(name="shamir-16^3x32-Ls16-mixedCG", dims=(16, 16, 16, 32), Ls=16, M5=1.8, m=0.01, eps=0.5,
                   seed=2, inner="f32", madwf=False, sample=(16, 16, 8, 2)),
     # the kernel-profiling case: every FP32 half-lattice field (509 MB) is larger than L2
     "hopprof": dict(name="shamir-24^3x48-Ls16-mixedCG", dims=(24, 24, 24, 48), Ls=16, M5=1.8, m=0.01, eps=0.5,
                     seed=2, inner="f32", madwf=False, sample=(24, 24, 6, 2)),
+    # operator-only case for kernel profiles: FP32 M_pc applications (the solvers' hop launches) on
+    # 20^3 x 24 x Ls=16; each FP32 half-lattice field (147 MB) is larger than L2, ~2.5 GB in all
+    "apply": dict(name="mpc-f32-shamir-20^3x24-Ls16", dims=(20, 20, 20, 24), Ls=16, M5=1.8, m=0.01, eps=0.5,
+                  seed=2, inner="f32", madwf=False, apply=True, sample=(20, 20, 4, 2)),
     # Hasenbusch ladder: Moebius 32^3 x 64 x Ls=16 (b = 1.5, c = 0.5), four Gaussian sources at the
     # masses {0.001, 0.01, 0.05, 0.2}, solved together by the multi-right-hand-side CG
     "ladder": dict(name="ladder-mobius-32^3x64-Ls16-4rhs", dims=(32, 32, 32, 64), Ls=16, M5=1.8,
@@ -74,7 +83,8 @@ WORKLOADS = {
 # FP64 CG iterations to 1e-10 on each input (GB300, dwf_cg inner=f64; for the ladder
 # the summed iterations of its four mixed-precision solves); they scale the
 # per-iteration oracle time of the reference arm when the FP64 solve is not run.
-FP64_ITERS = {"madwf": 300, "mixed": 250, "hopprof": 260, "ladder": 1180}
+FP64_ITERS = {"madwf": 300, "mixed": 250, "hopprof": 260, "ladder": 1180,
+              "apply": 0.5}  # the apply workload's unit is one M_pc application, half an iteration's work
 
 
 def parse():
@@ -86,11 +96,22 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--inner", default=None, choices=["f32", "f16"], help="inner precision (default per workload)")
     ap.add_argument("--study", action="store_true", help="sweep the MADWF settings (madwf workload)")
+    ap.add_argument("--md-study", action="store_true", help="FGI against Omelyan trajectories on the force workload")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 CG comparison solve")
     ap.add_argument("--no-extras", action="store_true", help="skip the precision comparison and the ladder")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tol", type=float, default=1e-10)
     return ap.parse_args()
+
+
+def hop_kernel_name(prec, batch=1):
+    """The hop kernel the library launches for this storage precision: the FP32
+    single-right-hand-side fast path, else the general slice-pair kernel."""
+    if prec == "f32" and batch == 1:
+        return ("hopf_kernel (FP32 Wilson hop at every s on slice pairs, bulk-copy staging, fused "
+                "fifth-dimension epilogues)")
+    return (f"hop3_kernel<{prec}>" + (f" batched over {batch} right-hand sides" if batch > 1 else "")
+            + " (Wilson hop at every s on slice pairs, fused fifth-dimension epilogues)")
 
 
 def hop_traffic(bytes_per_launch):
@@ -216,6 +237,11 @@ def config_of(w, inner):
         if inner == "f32":  # the library's trigger for the FP32 intermediate solves (include/dwf.h)
             c.update({"reliable_update_delta_pv": min(DELTA, max(math.sqrt(w["tol_pv"]), 1e-3)),
                       "reliable_update_delta_mob": min(DELTA, max(math.sqrt(w["tol_mob"]), 1e-3))})
+        c["madwf_settings"] = "fastest of the --study sweep on this input"
+        c["note"] = ("on these near-identity links plain mixed-precision CG (mixed_cg) is faster than MADWF: the "
+                     "direct solve needs only ~300 iterations, so the Pauli-Villars solves of a pass cost more than "
+                     "the final solve saves; MADWF gains where direct CG needs many more iterations (rough fields "
+                     "at light mass; the paper's direct solve took 11290)")
     if w.get("ladder"):
         c.update({"m_f": list(w["masses"]), "b": w["b5"], "c": w["c5"], "nrhs": len(w["masses"]),
                   "sources": f"Gaussian, seeds {w['seed']}..{w['seed'] + len(w['masses']) - 1}"})
@@ -414,13 +440,42 @@ def precision_comparison(dev, stream, hbm_peak, peak_src, tol):
         kt = lat.kernel_time(prec)
         lat.set_kernel_timing(False)
         kernel = "hop_kernel<f64> (FP64 Wilson hop; bound by the FP64 pipe, not HBM)" if prec == "f64" else \
-            f"hop3_kernel<{prec}> (Wilson hop at every s with fused fifth-dimension epilogues)"
+            hop_kernel_name(prec)
         rf = roofline(kt, hbm_peak, peak_src, kernel)
         if prec == "f64":
             rf["bound"] = "fp64-alu"
         out[prec] = {"seconds": e0.elapsed_time(e1) / 1e3, "iters": r.stats["iters"],
                      "reliable_updates": r.stats["reliable_updates"], "true_resid": r.stats["true_resid"],
                      "hop": rf}
+    lat.close()
+    return out
+
+
+def trajectory_timing(dev, stream):
+    """One force-gradient trajectory on the 16^3 x 8 x Ls=16 force workload
+    (quotient terms (0.01, 0.1) and (0.1, 1.0), length 0.4 in 4 steps, FP32
+    inner solves with FP64 reliable updates to 1e-10), after one warm-up
+    trajectory: time, force evaluations, solver iterations and dH."""
+    import torch
+
+    from paper_1111_5059_gb300 import dwf, inputs
+
+    dims, Ls = (16, 16, 16, 8), 16
+    terms = [(0.01, 0.1), (0.1, 1.0)]
+    U0 = torch.from_numpy(inputs.gauge_field(4, dims, 0.5)).to(dev)
+    p0 = torch.from_numpy(inputs.gaussian_momenta(4, dims)).to(dev)
+    phis = [torch.from_numpy(inputs.gaussian_spinor(50 + k, dims, Ls)).to(dev) for k in range(2)]
+    lat = dwf.Lattice(dims, Ls, 1.8, 1.0, 0.0, 1, stream=stream, device=dev)
+    out = {"workload": "force-shamir-16^3x8-Ls16-2terms", "integrator": "fgi", "tau": 0.1, "nsteps": 4}
+    for rep in range(2):
+        U, p = U0.clone(), p0.clone()
+        e0, e1 = _events(2)
+        e0.record(stream)
+        H0, H1, st, nf = dwf.md_trajectory(lat, terms, phis, U, p, 0.1, 4, tol=1e-10, inner="f32", delta=DELTA)
+        e1.record(stream)
+        e1.synchronize()
+        out.update({"seconds": e0.elapsed_time(e1) / 1e3, "force_evaluations": nf, "cg_iters": st["iters"],
+                    "dH": H1 - H0})
     lat.close()
     return out
 
@@ -561,9 +616,7 @@ def run_ladder(args, w, inner, world, rank, local, dev, hbm_peak, peak_src):
     del seq
 
     st, info = stats[-1], infos[-1]
-    roof = roofline(kt, hbm_peak, peak_src,
-                    f"hop3_kernel<{inner}> batched over right-hand sides (Wilson hop at every s, fused "
-                    "fifth-dimension epilogues per mass)",
+    roof = roofline(kt, hbm_peak, peak_src, hop_kernel_name(inner, info["batch"]),
                     {"traffic": hop_traffic(kt["bytes"] / max(1, kt["launches"])) if inner == "f32" else None,
                      "timed_launches": "the eager first iteration of each batch (graph replays are not bracketed "
                                        "by events)"})
@@ -617,27 +670,42 @@ def run_madwf_study(args, w, dev):
         return mobs[alpha]
 
     base_alpha = w["Ls"] / Lp
-    grid = [(0, None, None, base_alpha)]
+    grid = [(w["eps"], 0, None, None, base_alpha)]
     for n_dc in (1, 2, 3):
         for tol_pv in (1e-4, 1e-5, 1e-6):
             for tol_mob in (1e-3, 1e-4, 1e-5):
-                grid.append((n_dc, tol_pv, tol_mob, base_alpha))
+                grid.append((w["eps"], n_dc, tol_pv, tol_mob, base_alpha))
+    for tol_pv, tol_mob in ((1e-3, 1e-3), (1e-3, 1e-2), (1e-4, 1e-2), (3e-4, 3e-3)):
+        grid.append((w["eps"], 1, tol_pv, tol_mob, base_alpha))
     for alpha in (2.0, 3.2):
-        grid.append((w["n_dc"], w["tol_pv"], w["tol_mob"], alpha))
-        grid.append((1, 1e-5, 1e-4, alpha))
+        grid.append((w["eps"], 3, 1e-6, 1e-5, alpha))
+        grid.append((w["eps"], 1, 1e-5, 1e-4, alpha))
+    # the regime where the direct solve gets expensive: rougher links, same lattice and mass
+    for eps in (0.9, 1.2):
+        grid += [(eps, 0, None, None, base_alpha), (eps, 1, 1e-4, 1e-3, base_alpha),
+                 (eps, 2, 1e-4, 1e-3, base_alpha), (eps, 2, 1e-5, 1e-4, base_alpha)]
     lat.cg(w["m"], b, tol=args.tol, inner="f32", delta=DELTA, check_every=10, out=x)  # warm-up
-    for n_dc, tol_pv, tol_mob, alpha in grid:
+    cur_eps = w["eps"]
+    for eps, n_dc, tol_pv, tol_mob, alpha in grid:
+        if eps != cur_eps:
+            U = torch.from_numpy(inputs.gauge_field(w["seed"], w["dims"], eps)).to(dev)
+            lat.set_gauge(U)
+            for mb in mobs.values():
+                mb.set_gauge(U)
+            cur_eps = eps
         e0, e1 = _events(2)
         e0.record(stream)
         if n_dc == 0:
-            r = lat.cg(w["m"], b, tol=args.tol, inner="f32", delta=DELTA, check_every=10, out=x)
+            r = lat.cg(w["m"], b, tol=args.tol, inner="f32", delta=DELTA, check_every=10, out=x, max_iter=30000,
+                       raise_on_fail=False)
         else:
             r = dwf.madwf_solve(lat, mobius(alpha), w["m"], b, n_dc=n_dc, tol_pv=tol_pv, tol_mob=tol_mob,
-                                tol_final=args.tol, inner_prec="f32", delta=DELTA, check_every=10, out=x)
+                                tol_final=args.tol, inner_prec="f32", delta=DELTA, check_every=10, out=x,
+                                max_iter=30000, raise_on_fail=False)
         e1.record(stream)
         e1.synchronize()
-        row = {"study": "madwf", "n_dc": n_dc, "tol_pv": tol_pv, "tol_mob": tol_mob, "b_plus_c": alpha,
-               "seconds": e0.elapsed_time(e1) / 1e3}
+        row = {"study": "madwf", "eps": eps, "n_dc": n_dc, "tol_pv": tol_pv, "tol_mob": tol_mob, "b_plus_c": alpha,
+               "seconds": e0.elapsed_time(e1) / 1e3, "status": r.status}
         if n_dc == 0:
             row.update({"op_count": {"final": r.stats["op_count"], "total": r.stats["op_count"]},
                         "iters": {"final": r.stats["iters"]}, "true_resid": r.stats["true_resid"]})
@@ -651,6 +719,100 @@ def run_madwf_study(args, w, dev):
         print(json.dumps(row), flush=True)
     for m in mobs.values():
         m.close()
+    lat.close()
+
+
+def run_apply(args, w, world, rank, local, dev, hbm_peak, peak_src):
+    """Operator-only workload: one step is 10 applications of M_pc (and 10 of
+    M_pc^+) with FP32-stored fields through dwf_apply_Mpc_prec, the solvers'
+    own hop launches; the line's value is the time per M_pc application and its
+    roofline the FP32 hop's."""
+    import torch
+
+    from paper_1111_5059_gb300 import dwf, inputs
+
+    U = torch.from_numpy(inputs.gauge_field(w["seed"], w["dims"], w["eps"])).to(dev)
+    x = torch.from_numpy(inputs.gaussian_spinor(w["seed"], w["dims"], w["Ls"])).to(dev)
+    y = torch.empty_like(x)
+    stream = torch.cuda.current_stream(dev)
+    lat = dwf.Lattice(w["dims"], w["Ls"], w["M5"], 1.0, 0.0, 1, stream=stream, device=dev)
+    lat.set_gauge(U)
+    del U
+    reps = 10
+
+    def step():
+        for _ in range(reps):
+            lat.apply_Mpc_prec(w["m"], x, prec="f32", out=y)
+            lat.apply_Mpc_prec(w["m"], x, prec="f32", dag=True, out=y)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    lat.set_kernel_timing(True)
+    n0 = lat.launch_count()
+    step_ms = []
+    barrier(world)
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            e0, e1 = _events(2)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+    barrier(world)
+    launches = lat.launch_count() - n0
+    kt = lat.kernel_time("f32")
+    lat.set_kernel_timing(False)
+    ms_step = max_over_ranks(world, sum(step_ms), dev) / args.steps
+    value = ms_step / 1e3 / (2 * reps) / world
+    roof = roofline(kt, hbm_peak, peak_src, "hopf_kernel<8, ...> (FP32 fast path, Lh = 8)",
+                    {"share_of_step": kt["ms"] / max(1e-9, sum(step_ms))})
+    line = {"metric": "FP32 M_pc application time (two Wilson hops with fused fifth-dimension operators)",
+            "value": value, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w["name"], "lattice": "x".join(map(str, w["dims"])), "Ls": w["Ls"],
+                       "m": w["m"], "eps": w["eps"], "applications_per_step": 2 * reps,
+                       "l2": "each FP32 half-lattice field (147 MB) is larger than L2"},
+            "roofline": roof, "gpu_launches": launches, "clocks": clk.summary()}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    lat.close()
+
+
+def run_md_study(args, dev):
+    """Force-gradient against Omelyan trajectories (Sec. 2) on the force workload:
+    Shamir 16^3 x 8 x Ls=16, quotient terms (0.01, 0.1) and (0.1, 1.0), eps = 0.5,
+    Gaussian momenta and pseudofermion sources (seed 4), trajectory length 0.4 at
+    several step sizes: one JSON line each with dH, the force evaluations, the
+    solver iterations and the time.  Force solves: FP32 inner CG with FP64
+    reliable updates to 1e-10."""
+    import torch
+
+    from paper_1111_5059_gb300 import dwf, inputs
+
+    dims, Ls, M5 = (16, 16, 16, 8), 16, 1.8
+    terms = [(0.01, 0.1), (0.1, 1.0)]
+    U0 = torch.from_numpy(inputs.gauge_field(4, dims, 0.5)).to(dev)
+    p0 = torch.from_numpy(inputs.gaussian_momenta(4, dims)).to(dev)
+    phis = [torch.from_numpy(inputs.gaussian_spinor(50 + k, dims, Ls)).to(dev) for k in range(2)]
+    stream = torch.cuda.current_stream(dev)
+    lat = dwf.Lattice(dims, Ls, M5, 1.0, 0.0, 1, stream=stream, device=dev)
+    length = 0.4
+    for integ in ("fgi", "omelyan"):
+        for n in (1, 2, 4, 8):
+            U, p = U0.clone(), p0.clone()
+            e0, e1 = _events(2)
+            e0.record(stream)
+            H0, H1, st, nf = dwf.md_trajectory(lat, terms, phis, U, p, length / n, n, integrator=integ, tol=1e-10,
+                                               inner="f32", delta=DELTA)
+            e1.record(stream)
+            e1.synchronize()
+            print(json.dumps({"study": "md", "workload": "force-shamir-16^3x8-Ls16-2terms", "integrator": integ,
+                              "tau": length / n, "nsteps": n, "length": length, "dH": H1 - H0, "H0": H0,
+                              "force_evaluations": nf, "cg_iters": st["iters"],
+                              "seconds": e0.elapsed_time(e1) / 1e3}), flush=True)
     lat.close()
 
 
@@ -673,10 +835,16 @@ def main():
 
         build.build()
     hbm_peak, peak_src = measured_peak()
+    if args.md_study:
+        run_md_study(args, dev)
+        return
     if args.study:
         if not w["madwf"]:
             raise SystemExit("--study needs the madwf workload")
         run_madwf_study(args, w, dev)
+        return
+    if w.get("apply"):
+        run_apply(args, w, world, rank, local, dev, hbm_peak, peak_src)
         return
     if w.get("ladder"):
         run_ladder(args, w, inner, world, rank, local, dev, hbm_peak, peak_src)
@@ -781,8 +949,7 @@ def main():
                           "true_resid": rf.stats["true_resid"], "speedup_of_headline": secs / (ms_step / 1e3)}
             del rf
 
-    roof = roofline(kt, hbm_peak, peak_src,
-                    f"hop3_kernel<{inner}> (Wilson hop at every s with fused fifth-dimension epilogues)",
+    roof = roofline(kt, hbm_peak, peak_src, hop_kernel_name(inner),
                     {"traffic": hop_traffic(kt["bytes"] / max(1, kt["launches"])) if inner == "f32" else None,
                      "traffic_source": "ncu DRAM read+write per algorithmic byte on 24^3x48x16 Ls=16, scaled "
                                        "to this launch size (null: the kernel changed since it was measured)",
@@ -815,6 +982,8 @@ def main():
         line["precisions_16x32_Ls16"] = precision_comparison(dev, stream, hbm_peak, peak_src, args.tol)
         torch.cuda.empty_cache()
         line["ladder_32x64_Ls16"] = ladder_comparison(dev, stream, args.tol)
+        torch.cuda.empty_cache()
+        line["trajectory_16x8_Ls16"] = trajectory_timing(dev, stream)
     if rank == 0:
         if not args.no_cpu_baseline:
             iters = comp["fp64_cg"]["iters"] if "fp64_cg" in comp else FP64_ITERS[args.workload]

@@ -7,6 +7,13 @@
 // (the 4D Wilson hop inside D_DW, Sec. 4 Eq. dirac_eq, on one checkerboard,
 // with the fifth-dimension operators of the even-odd Schur form fused).
 //
+// Two kernels share the design below.  hopf_kernel (further down) is the
+// FP32 single-right-hand-side fast path for even Ls with Lh in {4, 6, 8, 16,
+// 32}: Lh fixed at compile time, each direction stage carrying its own links,
+// every slot refilled as soon as its data are in registers.  hop3_kernel is
+// the general one: FP16 storage, odd Ls, dense fifth-dimension fallbacks and
+// launches over several right-hand sides.
+//
 // GB300 design:
 //  * Thread (i, j) owns the slice pair (2j, 2j + 1) of 4D site i, so both
 //    lanes of every packed FP32x2 FMA (__ffma2_rn) use the same link element.
@@ -891,7 +898,9 @@ template <int LH> struct HopFShape {
   static constexpr int G = 32 / LH;
   static constexpr int BLK = 12 * LH * 16;                       // one site's FP32 spinor block
   static constexpr int LK_OFF = G * BLK;                         // the links of the stage's direction
-  static constexpr int SLOT = (LK_OFF + G * 80 + 127) / 128 * 128;
+  // 16-byte granularity (what the bulk copies need): rounding the slot up to
+  // 128 bytes made 16 warps' shared memory exceed the SM's at Lh = 8
+  static constexpr int SLOT = (LK_OFF + G * 80 + 15) / 16 * 16;
   static constexpr int NB_OFF = 2 * SLOT;                        // neighbour indices [2 groups][8][G]
   static constexpr int SMEM = NB_OFF + 2 * 8 * G * 4;
 };
@@ -964,7 +973,7 @@ __global__ void __launch_bounds__(32, MINB) hopf_kernel(const HopFArgs a) {
   issued += issue(g, 1, 1, 0);
   unsigned seq = 0;  // the stage being consumed: slot seq & 1, phase (seq >> 1) & 1
   bool bad = false;
-  double part = 0.0;
+  red[lane] = 0.0;  // this lane's partial sum of |out|^2 (kept out of the registers)
   int lb = 0;
   for (; g < a.ngroups; g += stride, lb ^= 1) {
     load_nb(g + stride, lb ^ 1);
@@ -972,14 +981,7 @@ __global__ void __launch_bounds__(32, MINB) hopf_kernel(const HopFArgs a) {
     const long left = a.Vh - h0;
     const int nact = left < G ? (int)left : G;
     const bool act = i < nact;
-    float2 ar[12], ai[12];
-    if (!HX) {
-#pragma unroll
-      for (int k = 0; k < 12; ++k) {
-        ar[k] = make_float2(0.f, 0.f);
-        ai[k] = ar[k];
-      }
-    }
+    float2 ar[12], ai[12];  // seeded by the site term (HX) or zeroed at the first direction
 #pragma unroll 1
     for (int t = 0; t < NST; ++t) {
       const int slot = seq & 1;
@@ -1026,6 +1028,15 @@ __global__ void __launch_bounds__(32, MINB) hopf_kernel(const HopFArgs a) {
         }
         __syncwarp();
         issued += k2 < NST ? issue(g, k2, slot, lb) : issue(g + stride, k2 - NST, slot, lb ^ 1);
+        if (!HX && t == 0) {
+          // zeroed here rather than before the stage loop: the accumulator is
+          // not live across the group's first wait and copy issue (fewer spills)
+#pragma unroll
+          for (int k = 0; k < 12; ++k) {
+            ar[k] = make_float2(0.f, 0.f);
+            ai[k] = ar[k];
+          }
+        }
         if (act) {
           switch (d & 3) {
             case 0: su3_accumulate<0>(sg, hr, hi, U, ar, ai); break;
@@ -1054,7 +1065,7 @@ __global__ void __launch_bounds__(32, MINB) hopf_kernel(const HopFArgs a) {
           p0 = fma2(ar[k], ar[k], p0);
           p1 = fma2(ai[k], ai[k], p1);
         }
-        part += (double)((p0.x + p0.y) + (p1.x + p1.y));
+        red[lane] += (double)((p0.x + p0.y) + (p1.x + p1.y));
       }
     }
   }
@@ -1066,7 +1077,6 @@ __global__ void __launch_bounds__(32, MINB) hopf_kernel(const HopFArgs a) {
     return;
   }
   if (a.partials) {
-    red[lane] = part;
     __syncwarp();
     if (lane == 0) {
       double t = 0.0;
@@ -1172,7 +1182,7 @@ static bool hopf_takes(const dwf_lattice* L, const HopCall& c, const HopBatch& b
   return eout.kind != 2;
 }
 
-template <int LH, int MINB>
+template <int LH, int MINB0, int MINB1>
 static dwf_status hopf_t(dwf_lattice* L, const HopCall& c, const HopBatch& b, const SOpK<float>& ex,
                          const SOpK<float>& eout, int ctas_per_sm) {
   typedef HopFShape<LH> Sh;
@@ -1204,21 +1214,22 @@ static dwf_status hopf_t(dwf_lattice* L, const HopCall& c, const HopBatch& b, co
     if (c.nblocks) *c.nblocks = (int)grid;
     return DWF_OK;
   };
-  if (c.dag) return c.has_x ? run(hopf_kernel<LH, 1, 1, MINB>) : run(hopf_kernel<LH, 1, 0, MINB>);
-  return c.has_x ? run(hopf_kernel<LH, 0, 1, MINB>) : run(hopf_kernel<LH, 0, 0, MINB>);
+  if (c.dag) return c.has_x ? run(hopf_kernel<LH, 1, 1, MINB1>) : run(hopf_kernel<LH, 1, 0, MINB0>);
+  return c.has_x ? run(hopf_kernel<LH, 0, 1, MINB1>) : run(hopf_kernel<LH, 0, 0, MINB0>);
 }
 
 dwf_status launch_hop2(dwf_lattice* L, const HopCall& c, const HopBatch& b, const SOpK<float>* ex,
                        const SOpK<float>* eout, int G, int ctas_per_sm) {
   if (hopf_takes(L, c, b, ex[0], eout[0])) {
-    // resident warps per SM as measured best on GB300: 16 (128 registers) for
-    // Lh = 6 and 8, 12 (168 registers) where the epilogue scan is longer
+    // resident warps per SM (without / with a site term) as measured best on
+    // GB300: 16 (128 registers) or 12 (168 registers); at Lh = 16 the hop
+    // with a site term ran 11 % slower when held to 128 registers
     switch (L->Lh) {
-      case 4: return hopf_t<4, 12>(L, c, b, ex[0], eout[0], ctas_per_sm);
-      case 6: return hopf_t<6, 16>(L, c, b, ex[0], eout[0], ctas_per_sm);
-      case 8: return hopf_t<8, 16>(L, c, b, ex[0], eout[0], ctas_per_sm);
-      case 16: return hopf_t<16, 12>(L, c, b, ex[0], eout[0], ctas_per_sm);
-      default: return hopf_t<32, 12>(L, c, b, ex[0], eout[0], ctas_per_sm);
+      case 4: return hopf_t<4, 12, 12>(L, c, b, ex[0], eout[0], ctas_per_sm);
+      case 6: return hopf_t<6, 16, 16>(L, c, b, ex[0], eout[0], ctas_per_sm);
+      case 8: return hopf_t<8, 16, 16>(L, c, b, ex[0], eout[0], ctas_per_sm);
+      case 16: return hopf_t<16, 16, 12>(L, c, b, ex[0], eout[0], ctas_per_sm);
+      default: return hopf_t<32, 12, 12>(L, c, b, ex[0], eout[0], ctas_per_sm);
     }
   }
   if (b.in[0].prec == DWF_F32) return hop3_t<float>(L, c, b, ex, eout, G, ctas_per_sm);

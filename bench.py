@@ -104,6 +104,21 @@ def parse():
     return ap.parse_args()
 
 
+def host_copy(dwf, arr):
+    """A page-locked, huge-page-backed host copy of a numpy array
+    (dwf.host_empty): the host side of the end-to-end copies."""
+    import torch
+
+    t = dwf.host_empty(arr.shape)
+    t.copy_(torch.from_numpy(arr))
+    return t
+
+
+HOST_BUFFERS = ("page-locked host buffers from dwf_host_alloc (transparent huge pages, cudaHostRegister): "
+                "with base pages the first copy after a solve ran at 6-50 GB/s while the host-page "
+                "translations were fetched again")
+
+
 def hop_kernel_name(prec, batch=1):
     """The hop kernel the library launches for this storage precision: the FP32
     single-right-hand-side fast path, else the general slice-pair kernel."""
@@ -529,10 +544,9 @@ def run_ladder(args, w, inner, world, rank, local, dev, hbm_peak, peak_src):
     masses = w["masses"]
     n = len(masses)
     U = torch.from_numpy(inputs.gauge_field(w["seed"], w["dims"], w["eps"])).to(dev)
-    b_host = [torch.from_numpy(inputs.gaussian_spinor(w["seed"] + r, w["dims"], w["Ls"])).pin_memory()
-              for r in range(n)]
+    b_host = [host_copy(dwf, inputs.gaussian_spinor(w["seed"] + r, w["dims"], w["Ls"])) for r in range(n)]
     bs = [h.to(dev) for h in b_host]
-    x_host = [torch.empty_like(h).pin_memory() for h in b_host]
+    x_host = [dwf.host_empty(h.shape) for h in b_host]
     stream = torch.cuda.current_stream(dev)
     lat = dwf.Lattice(w["dims"], w["Ls"], w["M5"], w["b5"], w["c5"], 1, stream=stream, device=dev)
     lat.set_gauge(U)
@@ -631,7 +645,7 @@ def run_ladder(args, w, inner, world, rank, local, dev, hbm_peak, peak_src):
             "data": "synthetic", "config": config_of(w, inner), "roofline": roof,
             "e2e": {"value": e2e_ms / 1e3 / world, "unit": "s",
                     "h2d_bytes_per_step": sum(h.numel() * 16 for h in b_host),
-                    "d2h_bytes_per_step": sum(h.numel() * 16 for h in x_host)},
+                    "d2h_bytes_per_step": sum(h.numel() * 16 for h in x_host), "host_buffers": HOST_BUFFERS},
             "gpu_launches": launches, "solve": solve_info, "sequential_cg": sequential,
             "all_rhs_one_launch": one_launch, "clocks": clk.summary()}
     if rank == 0:
@@ -855,10 +869,10 @@ def main():
         return
 
     U = torch.from_numpy(inputs.gauge_field(w["seed"], w["dims"], w["eps"])).to(dev)
-    b_host = torch.from_numpy(inputs.gaussian_spinor(w["seed"], w["dims"], w["Ls"])).pin_memory()
+    b_host = host_copy(dwf, inputs.gaussian_spinor(w["seed"], w["dims"], w["Ls"]))
     b = b_host.to(dev)
     x = torch.empty_like(b)
-    x_host = torch.empty(b_host.shape, dtype=b_host.dtype, pin_memory=True)
+    x_host = dwf.host_empty(b_host.shape)
     stream = torch.cuda.current_stream(dev)
     lat = dwf.Lattice(w["dims"], w["Ls"], w["M5"], 1.0, 0.0, 1, stream=stream, device=dev)
     lat.set_gauge(U)
@@ -971,7 +985,7 @@ def main():
             "e2e": {"value": e2e_ms / 1e3 / world, "unit": "s", "h2d_bytes_per_step": nbytes,
                     "d2h_bytes_per_step": nbytes, "h2d_ms": h2d_ms, "solve_ms": statistics.mean(e[2] for e in e2e),
                     "d2h_ms": d2h_ms, "h2d_gbs": nbytes / (h2d_ms / 1e3) / 1e9 if h2d_ms > 0 else None,
-                    "d2h_gbs": nbytes / (d2h_ms / 1e3) / 1e9 if d2h_ms > 0 else None},
+                    "d2h_gbs": nbytes / (d2h_ms / 1e3) / 1e9 if d2h_ms > 0 else None, "host_buffers": HOST_BUFFERS},
             "gpu_launches": launches, "solve": solve_info, "clocks": clk.summary()}
     line.update(comp)
     for L in lats:

@@ -289,6 +289,24 @@ dwf_status dwf_md_trajectory(dwf_lattice_t h, int nterms, const dwf_quotient* te
 #define DWF_NOALLOC_SCRATCH_BYTES (32u << 20)
 dwf_status dwf_apply_Mpc_noalloc(dwf_lattice_t h, double m, int dag, const void* in, void* out);
 
+/* Page-locked HOST memory for the host side of copies to and from the GPU
+ * (the paper has no counterpart): bytes (> 0) of zeroed host memory, mapped
+ * on a huge-page boundary, advised for transparent huge pages and
+ * registered with the CUDA driver (cudaHostRegister).  Each copy between the
+ * GPU and page-locked memory translates the host pages it touches; with the
+ * host's base pages a multi-GB buffer is tens of thousands of pages, and the
+ * first copy after other GPU work runs several times slower while their
+ * translations are fetched again, which huge pages avoid.  Where the host
+ * kernel has transparent huge pages off the memory is still page-locked,
+ * without that gain.  *ptr receives the buffer (NULL on error); the caller
+ * owns it and releases it with dwf_host_free.  Errors (dwf_last_error(NULL)):
+ * DWF_ERR_INVALID_ARG for a NULL ptr or zero bytes, DWF_ERR_OOM if the
+ * mapping fails, DWF_ERR_CUDA if registration fails (e.g. no GPU).
+ * dwf_host_free(NULL) is a no-op; a pointer that dwf_host_alloc did not
+ * return gives DWF_ERR_INVALID_ARG. */
+dwf_status dwf_host_alloc(size_t bytes, void** ptr);
+dwf_status dwf_host_free(void* ptr);
+
 /* Instrumentation (no counterpart in the paper; used to measure the Wilson
  * hop kernels against the HBM roofline).  With timing enabled every hop
  * launch on the handle's stream is bracketed by CUDA events.

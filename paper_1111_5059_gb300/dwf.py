@@ -9,6 +9,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import weakref
 from dataclasses import dataclass
 
 import torch
@@ -107,6 +108,8 @@ def _declare(lib):
                          ctypes.POINTER(MultiInfo)],
         "madwf_solve": [H, H, ctypes.c_double, _VP, _VP, ctypes.POINTER(MadwfParams), ctypes.POINTER(MadwfStats)],
         "dwf_apply_Mpc_noalloc": [H, ctypes.c_double, ctypes.c_int, _VP, _VP],
+        "dwf_host_alloc": [ctypes.c_size_t, ctypes.POINTER(_VP)],
+        "dwf_host_free": [_VP],
         "dwf_force": [H, ctypes.c_int, ctypes.POINTER(Quotient), ctypes.POINTER(_VP), ctypes.POINTER(_VP), _VP, _VP,
                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(CGParams), ctypes.POINTER(Stats)],
         "dwf_action": [H, ctypes.c_int, ctypes.POINTER(Quotient), ctypes.POINTER(_VP), ctypes.POINTER(CGParams),
@@ -151,6 +154,25 @@ def _check(status: int, handle=None):
     if status != 0:
         msg = lib().dwf_last_error(handle).decode(errors="replace")
         raise DWFError(status, msg)
+
+
+def host_empty(shape, dtype=torch.complex128) -> torch.Tensor:
+    """A page-locked host tensor from dwf_host_alloc (huge-page backed; see
+    include/dwf.h): the host side of copies to and from the GPU.  The memory
+    is released when the returned tensor and every view of it are gone."""
+    numel = 1
+    for n in shape:
+        numel *= int(n)
+    nbytes = numel * torch.empty((), dtype=dtype).element_size()
+    # torch reports registered host memory as pinned only once its own CUDA
+    # state is initialised
+    torch.cuda.init()
+    p = _VP()
+    _check(lib().dwf_host_alloc(nbytes, ctypes.byref(p)))
+    buf = (ctypes.c_char * nbytes).from_address(p.value)
+    weakref.finalize(buf, lib().dwf_host_free, _VP(p.value))
+    # torch.frombuffer keeps `buf` alive for as long as the tensor's storage
+    return torch.frombuffer(buf, dtype=dtype, count=numel).view(tuple(shape))
 
 
 def _ptr(t: torch.Tensor, shape=None, dtype=torch.complex128) -> int:

@@ -149,6 +149,8 @@ def test_null_handle_is_rejected_by_every_entry_point(lib):
         ("dwf_set_wait_limit", lambda: L.dwf_set_wait_limit(None, 0), "dwf_set_wait_limit:"),
         ("dwf_md_trajectory", lambda: L.dwf_md_trajectory(None, 1, None, None, None, None, 0.1, 1, 0, 1, None, None,
                                                           None, None, None), "dwf_md_trajectory:"),
+        # not a handle, but the same rule for the host allocator's pointer argument
+        ("dwf_host_alloc", lambda: L.dwf_host_alloc(64, None), "dwf_host_alloc:"),
     ]
     for name, call, prefix in calls:
         assert call() == 1, name
@@ -156,4 +158,16 @@ def test_null_handle_is_rejected_by_every_entry_point(lib):
     # every entry point of the header is covered
     hdr = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "dwf.h")).read(), flags=re.S)
     declared = set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*((?:dwf|madwf|fgi)_\w+)\s*\(", hdr, flags=re.M))
-    assert declared == {n for n, _, _ in calls} | {"dwf_destroy_lattice", "dwf_last_error"}
+    assert declared == {n for n, _, _ in calls} | {"dwf_destroy_lattice", "dwf_last_error", "dwf_host_free"}
+
+
+def test_host_allocator_rejects_bad_arguments(lib):
+    L, dwf = lib
+    p = ctypes.c_void_p(12345)
+    assert L.dwf_host_alloc(0, ctypes.byref(p)) == 1
+    assert p.value is None
+    assert "zero bytes" in L.dwf_last_error(None).decode()
+    assert L.dwf_host_free(None) == 0
+    buf = ctypes.create_string_buffer(64)
+    assert L.dwf_host_free(ctypes.cast(buf, ctypes.c_void_p)) == 1
+    assert "not a dwf_host_alloc pointer" in L.dwf_last_error(None).decode()

@@ -197,12 +197,17 @@ extern "C" dwf_status madwf_solve(dwf_lattice_t L, dwf_lattice_t Li, double m, c
   dwf_status status = DWF_OK;
   if (bnorm > 0.0) {
     for (int pass = 0; pass < prm->n_dc; ++pass) {
-      // r = b - D(m) x
-      DWF_TRY(apply_D(L, ops_m, false, xe, xo, re, ro));
-      DWF_TRY(blas_axpby(L, 1.0, be, -1.0, re));
-      DWF_TRY(blas_axpby(L, 1.0, bo, -1.0, ro));
-      double rn;
-      DWF_TRY(norm_pair(L, re, ro, &rn));
+      // r = b - D(m) x  (x = 0 on the first pass: r = b)
+      double rn = bnorm;
+      if (pass == 0) {
+        DWF_TRY(blas_copy(L, be, re));
+        DWF_TRY(blas_copy(L, bo, ro));
+      } else {
+        DWF_TRY(apply_D(L, ops_m, false, xe, xo, re, ro));
+        DWF_TRY(blas_axpby(L, 1.0, be, -1.0, re));
+        DWF_TRY(blas_axpby(L, 1.0, bo, -1.0, ro));
+        DWF_TRY(norm_pair(L, re, ro, &rn));
+      }
       if (pass > 0) st.pass_resid[pass - 1] = rn / bnorm;
       if (rn <= prm->tol_final * bnorm) break;
       // 1. c = P^-1 D(1)^-1 r

@@ -51,10 +51,12 @@ HBM_NOMINAL_GBS = 7900.0  # GB300 HBM3e data-sheet bandwidth, reported beside th
 # recomputed when the iterated one has dropped by this factor
 DELTA = 0.01
 
-# DRAM traffic per algorithmic byte of the FP32 hop kernel, from one ncu
-# capture (dram__bytes_read.sum + dram__bytes_write.sum of two launches on the
-# 24^3x48x16 Ls=16 case); it applies only to the kernel source it was taken on.
-HOP_TRAFFIC = {"source_sha256_prefix": "dc5de73caaafee4b", "ratio": 1.105}
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per algorithmic
+# byte of the FP32 hop kernel, by slice pairs per 4D site (Lh), from ncu
+# captures of the apply workloads (four launches each: M_pc and M_pc^+
+# applications); they hold only for the kernel source they were taken on.
+HOP_TRAFFIC = {"source_sha256_prefix": "9a3c6a302ef70cb9", "ratio_by_lh": {8: 1.0286, 16: 1.0459, 6: 1.1658},
+               "captures": "apply (Lh 8), apply-ls32 (Lh 16), apply-mobius-ls12 (Lh 6)"}
 
 WORKLOADS = {
     # MADWF: Shamir 24^3 x 64 x Ls=32, m_f = 0.002, eps = 0.6, through Moebius Ls' = 12 with
@@ -74,6 +76,13 @@ WORKLOADS = {
     # 20^3 x 24 x Ls=16; each FP32 half-lattice field (147 MB) is larger than L2, ~2.5 GB in all
     "apply": dict(name="mpc-f32-shamir-20^3x24-Ls16", dims=(20, 20, 20, 24), Ls=16, M5=1.8, m=0.01, eps=0.5,
                   seed=2, inner="f32", madwf=False, apply=True, sample=(20, 20, 4, 2)),
+    # the same at the headline's fifth-dimension shapes (Shamir Ls = 32, Moebius Ls' = 12), for
+    # profiling the kernels the headline solve runs; each FP32 half-lattice field exceeds L2
+    "apply-ls32": dict(name="mpc-f32-shamir-16^3x32-Ls32", dims=(16, 16, 16, 32), Ls=32, M5=1.8, m=0.002,
+                       eps=0.6, seed=3, inner="f32", madwf=False, apply=True, sample=(16, 16, 4, 2)),
+    "apply-mobius-ls12": dict(name="mpc-f32-mobius-24^3x32-Ls12", dims=(24, 24, 24, 32), Ls=12, M5=1.8, m=0.002,
+                              eps=0.6, seed=3, inner="f32", madwf=False, apply=True, b5=11 / 6, c5=5 / 6,
+                              sample=(24, 24, 4, 2)),
     # Hasenbusch ladder: Moebius 32^3 x 64 x Ls=16 (b = 1.5, c = 0.5), four Gaussian sources at the
     # masses {0.001, 0.01, 0.05, 0.2}, solved together by the multi-right-hand-side CG
     "ladder": dict(name="ladder-mobius-32^3x64-Ls16-4rhs", dims=(32, 32, 32, 64), Ls=16, M5=1.8,
@@ -84,7 +93,8 @@ WORKLOADS = {
 # the summed iterations of its four mixed-precision solves); they scale the
 # per-iteration oracle time of the reference arm when the FP64 solve is not run.
 FP64_ITERS = {"madwf": 300, "mixed": 250, "hopprof": 260, "ladder": 1180,
-              "apply": 0.5}  # the apply workload's unit is one M_pc application, half an iteration's work
+              "apply": 0.5, "apply-ls32": 0.5, "apply-mobius-ls12": 0.5}
+# (an apply workload's unit is one M_pc application, half an iteration's work)
 
 
 def parse():
@@ -129,9 +139,11 @@ def hop_kernel_name(prec, batch=1):
             + " (Wilson hop at every s on slice pairs, fused fifth-dimension epilogues)")
 
 
-def hop_traffic(bytes_per_launch):
-    """DRAM bytes per launch of the FP32 hop (scaled from the ncu capture), or
-    None if the kernel source differs from the one that was measured."""
+def hop_traffic(parts, launches):
+    """DRAM bytes per launch of the FP32 hop: the algorithmic bytes of each
+    lattice's launches (parts: [(Ls, bytes)]) times the measured ratio at its
+    Lh, over the launches; None if the kernel source differs from the one
+    that was measured or an Lh was not measured."""
     import hashlib
 
     try:
@@ -139,9 +151,20 @@ def hop_traffic(bytes_per_launch):
             sha = hashlib.sha256(f.read()).hexdigest()[:16]
     except OSError:
         return None
-    if sha != HOP_TRAFFIC["source_sha256_prefix"]:
+    if sha != HOP_TRAFFIC["source_sha256_prefix"] or launches < 1:
         return None
-    return bytes_per_launch * HOP_TRAFFIC["ratio"]
+    total = 0.0
+    for Ls, nbytes in parts:
+        r = HOP_TRAFFIC["ratio_by_lh"].get((Ls + 1) // 2)
+        if r is None:
+            return None
+        total += nbytes * r
+    return total / launches
+
+
+TRAFFIC_SOURCE = ("ncu DRAM read+write per algorithmic byte of the same kernel at the same Lh on a smaller "
+                  "lattice (apply workloads), times this run's algorithmic bytes (null: the kernel source "
+                  "changed since it was measured)")
 
 
 def measured_peak():
@@ -456,7 +479,9 @@ def precision_comparison(dev, stream, hbm_peak, peak_src, tol):
         lat.set_kernel_timing(False)
         kernel = "hop_kernel<f64> (FP64 Wilson hop; bound by the FP64 pipe, not HBM)" if prec == "f64" else \
             hop_kernel_name(prec)
-        rf = roofline(kt, hbm_peak, peak_src, kernel)
+        rf = roofline(kt, hbm_peak, peak_src, kernel,
+                      {"traffic": hop_traffic([(w["Ls"], kt["bytes"])], kt["launches"]), "traffic_source": TRAFFIC_SOURCE}
+                      if prec == "f32" else None)
         if prec == "f64":
             rf["bound"] = "fp64-alu"
         out[prec] = {"seconds": e0.elapsed_time(e1) / 1e3, "iters": r.stats["iters"],
@@ -631,7 +656,8 @@ def run_ladder(args, w, inner, world, rank, local, dev, hbm_peak, peak_src):
 
     st, info = stats[-1], infos[-1]
     roof = roofline(kt, hbm_peak, peak_src, hop_kernel_name(inner, info["batch"]),
-                    {"traffic": hop_traffic(kt["bytes"] / max(1, kt["launches"])) if inner == "f32" else None,
+                    {"traffic": hop_traffic([(w["Ls"], kt["bytes"])], kt["launches"])
+                     if inner == "f32" and info["batch"] == 1 else None, "traffic_source": TRAFFIC_SOURCE,
                      "timed_launches": "the eager first iteration of each batch (graph replays are not bracketed "
                                        "by events)"})
     solve_info = {"iters": [s["iters"] for s in st], "reliable_updates": [s["reliable_updates"] for s in st],
@@ -749,7 +775,7 @@ def run_apply(args, w, world, rank, local, dev, hbm_peak, peak_src):
     x = torch.from_numpy(inputs.gaussian_spinor(w["seed"], w["dims"], w["Ls"])).to(dev)
     y = torch.empty_like(x)
     stream = torch.cuda.current_stream(dev)
-    lat = dwf.Lattice(w["dims"], w["Ls"], w["M5"], 1.0, 0.0, 1, stream=stream, device=dev)
+    lat = dwf.Lattice(w["dims"], w["Ls"], w["M5"], w.get("b5", 1.0), w.get("c5", 0.0), 1, stream=stream, device=dev)
     lat.set_gauge(U)
     del U
     reps = 10
@@ -780,15 +806,17 @@ def run_apply(args, w, world, rank, local, dev, hbm_peak, peak_src):
     lat.set_kernel_timing(False)
     ms_step = max_over_ranks(world, sum(step_ms), dev) / args.steps
     value = ms_step / 1e3 / (2 * reps) / world
-    roof = roofline(kt, hbm_peak, peak_src, "hopf_kernel<8, ...> (FP32 fast path, Lh = 8)",
-                    {"share_of_step": kt["ms"] / max(1e-9, sum(step_ms))})
+    roof = roofline(kt, hbm_peak, peak_src, hop_kernel_name("f32") + f" at Lh = {(w['Ls'] + 1) // 2}",
+                    {"traffic": hop_traffic([(w["Ls"], kt["bytes"])], kt["launches"]),
+                     "traffic_source": TRAFFIC_SOURCE, "share_of_step": kt["ms"] / max(1e-9, sum(step_ms))})
     line = {"metric": "FP32 M_pc application time (two Wilson hops with fused fifth-dimension operators)",
             "value": value, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": w["name"], "lattice": "x".join(map(str, w["dims"])), "Ls": w["Ls"],
-                       "m": w["m"], "eps": w["eps"], "applications_per_step": 2 * reps,
-                       "l2": "each FP32 half-lattice field (147 MB) is larger than L2"},
+                       "b": w.get("b5", 1.0), "c": w.get("c5", 0.0), "m": w["m"], "eps": w["eps"],
+                       "applications_per_step": 2 * reps,
+                       "l2": "each FP32 half-lattice field is larger than L2 (129 MB)"},
             "roofline": roof, "gpu_launches": launches, "clocks": clk.summary()}
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -964,9 +992,8 @@ def main():
             del rf
 
     roof = roofline(kt, hbm_peak, peak_src, hop_kernel_name(inner),
-                    {"traffic": hop_traffic(kt["bytes"] / max(1, kt["launches"])) if inner == "f32" else None,
-                     "traffic_source": "ncu DRAM read+write per algorithmic byte on 24^3x48x16 Ls=16, scaled "
-                                       "to this launch size (null: the kernel changed since it was measured)",
+                    {"traffic": hop_traffic([(L.Ls, d["bytes"]) for L, d in zip(lats, kts)], kt["launches"])
+                     if inner == "f32" else None, "traffic_source": TRAFFIC_SOURCE,
                      "share_of_step": kt["ms"] / max(1e-9, sum(step_ms))})
     if w["madwf"]:
         solve_info = {"passes": st["passes"], "pass_resid": st["pass_resid"], "true_resid": true_res,

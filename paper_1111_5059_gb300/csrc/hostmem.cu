@@ -73,6 +73,13 @@ extern "C" dwf_status dwf_host_alloc(size_t bytes, void** ptr) {
   // fault every page in (each huge page on its first touch)
   volatile unsigned char* c = static_cast<volatile unsigned char*>(p);
   for (size_t off = 0; off < body; off += page) c[off] = 0;
+#ifndef MADV_COLLAPSE
+#define MADV_COLLAPSE 25
+#endif
+  // where a fault could not get a huge page (fragmented memory), ask the
+  // kernel to collapse the range synchronously; older kernels reject the
+  // advice, which changes nothing
+  madvise(p, body, MADV_COLLAPSE);
   const cudaError_t e = cudaHostRegister(p, body, cudaHostRegisterDefault);
   if (e != cudaSuccess) {
     munmap(p, body);

@@ -159,6 +159,12 @@ dwf_status dwf_cg_multi(dwf_lattice_t h, int nrhs, const double* masses, const v
  * guess to x; a final DWF solve to tol_final starts from that guess.  All
  * solves use CG on the normal equations at the `inner` precision with FP64
  * reliable updates; residuals and the accumulated solution stay FP64.
+ * With inner != DWF_F64, tol_pv >= 1e-5 and tol_mob >= 1e-4 the passes'
+ * Pauli-Villars and Moebius solves, and the operator applications that make
+ * their sources, compute their FP64-field Wilson hops in FP32 (FP32 links;
+ * inputs truncated to FP32): their results need only those tolerances, and
+ * GB300 runs FP64 arithmetic at ~1/70 of its FP32 rate.  The residual
+ * b - D x between passes, the final solve and x stay FP64.
  * `x` need not be initialised; b and x are whole-lattice boundary-layout
  * device spinors of the outer lattice.  Work runs on the outer handle's
  * stream.  Returns DWF_ERR_NOT_CONVERGED if the final solve hits max_iter
@@ -288,6 +294,15 @@ dwf_status dwf_md_trajectory(dwf_lattice_t h, int nterms, const dwf_quotient* te
  * (dwf_set_kernel_timing) is suspended during the call. */
 #define DWF_NOALLOC_SCRATCH_BYTES (32u << 20)
 dwf_status dwf_apply_Mpc_noalloc(dwf_lattice_t h, double m, int dag, const void* in, void* out);
+
+/* Arithmetic of the Wilson hops on FP64 fields (no counterpart in the
+ * paper): mode 0 (the default) FP64; mode 1 FP32 (FP32 links, inputs
+ * truncated to FP32, results widened exactly to FP64), for every FP64-field
+ * hop of the handle -- the dwf_apply_* operators, the FP64 steps of every
+ * solve.  A test and experimentation switch: madwf_solve uses the same
+ * arithmetic for its passes by itself (see there).  Errors:
+ * DWF_ERR_INVALID_ARG for a null handle or another mode. */
+dwf_status dwf_set_fp64_arithmetic(dwf_lattice_t h, int mode);
 
 /* Page-locked HOST memory for the host side of copies to and from the GPU
  * (the paper has no counterpart): bytes (> 0) of zeroed host memory, mapped

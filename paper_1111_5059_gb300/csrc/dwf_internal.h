@@ -263,6 +263,10 @@ struct dwf_lattice {
   // FP32 links direction-major per output parity, [8][Vh][20] floats (9 complex + 8 bytes of
   // padding: the 80-byte rows of consecutive sites are one contiguous, 16-byte aligned copy)
   float* links_dm[2] = {nullptr, nullptr};
+  // > 0: hops on FP64 fields compute in FP32 (hop.cu, hop_lp_kernel); set by
+  // Fp32StepScope around approximate steps, and by dwf_set_fp64_arithmetic
+  int fp64_in_fp32 = 0;
+  int fp64_arith = 0;  // dwf_set_fp64_arithmetic: 1 = every FP64-field hop in FP32
   bool gauge_set = false;
   std::deque<dwf::SOps> sops;  // deque: pointers stay valid on growth
   std::map<std::string, dwf::Buffer> ws;
@@ -357,6 +361,20 @@ struct HopCall {
   int* nblocks = nullptr;
 };
 dwf_status launch_hop(dwf_lattice* L, const HopCall& c);
+
+// Hops on FP64 fields compute in FP32 while one of these is alive (on)
+struct Fp32StepScope {
+  dwf_lattice* L;
+  bool on;
+  Fp32StepScope(dwf_lattice* l, bool o) : L(l), on(o) {
+    if (on) ++L->fp64_in_fp32;
+  }
+  ~Fp32StepScope() {
+    if (on) --L->fp64_in_fp32;
+  }
+  Fp32StepScope(const Fp32StepScope&) = delete;
+  Fp32StepScope& operator=(const Fp32StepScope&) = delete;
+};
 
 // One hop launch over several right-hand sides that share the links: the
 // fields and fifth-dimension operators (one mass each) come from the batch,

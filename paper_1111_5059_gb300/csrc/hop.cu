@@ -119,6 +119,126 @@ __global__ void __launch_bounds__(256) hop_kernel(const HopArgs<S> a) {
   }
 }
 
+// ---------------------------------------------------------------- FP64 fields, FP32 arithmetic
+//
+// The same hop on FP64-stored fields computed in FP32 (FP32 links), for the
+// operator applications and solves inside an approximate step whose result
+// needs only a few digits (the MADWF passes' Pauli-Villars and Moebius
+// solves and their sources).  GB300 converts between FP64 and FP32 at its
+// FP64 rate (about 1/70 of the FP32 rate), so the conversions use integer
+// operations: a load keeps the top 24 significand bits (truncation: relative
+// error below 2^-23; values below 2^-126 become zero) and a store widens the
+// FP32 result exactly.
+
+__device__ __forceinline__ float narrow_bits(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hw = (unsigned)(b >> 32), lw = (unsigned)b;
+  const unsigned sign = hw & 0x80000000u;
+  const int e = (int)((hw >> 20) & 0x7ffu);
+  if (e < 897) return __uint_as_float(sign);
+  if (e > 1150) return __uint_as_float(sign | 0x7f800000u | ((e == 2047 && ((hw & 0xfffffu) | lw)) ? 0x400000u : 0u));
+  return __uint_as_float(sign | ((unsigned)(e - 896) << 23) | ((hw & 0xfffffu) << 3) | (lw >> 29));
+}
+__device__ __forceinline__ double widen_bits(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned sign = u & 0x80000000u;
+  const unsigned e = (u >> 23) & 0xffu;
+  const unsigned m = u & 0x7fffffu;
+  unsigned hw;
+  if (e == 0) hw = sign;  // zero; FP32 subnormals are taken as zero
+  else if (e == 255) hw = sign | 0x7ff00000u | (m ? 0x80000u : 0u);
+  else hw = sign | ((e + 896u) << 20) | (m >> 3);
+  const unsigned lw = (e == 0 || e == 255) ? 0u : (m << 29);
+  return __longlong_as_double((long long)(((unsigned long long)hw << 32) | lw));
+}
+
+struct HopLPArgs {
+  const double* in;
+  double* out;
+  const double* x;     // nullptr: no site term
+  const float* links;  // FP32 [Vh][8][18]
+  const int* nbr;
+  long Vh;
+  int Ls, Lh, NS;
+  SOpK<float> ex, eout;
+  float scale, xscale;
+  double* partials;
+};
+
+__device__ __forceinline__ void load_narrow(const double* f, long h, int s, int Lh, float* v) {
+  const double* base = f + elem_index(h, 0, s >> 1, Lh) + (s & 1);
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    v[2 * k] = narrow_bits(__ldg(base + (long)k * Lh * 4));
+    v[2 * k + 1] = narrow_bits(__ldg(base + (long)k * Lh * 4 + 2));
+  }
+}
+
+template <int MU, int SG>
+__device__ __forceinline__ void dir_lp(const HopLPArgs& a, long h, int s, int d, float* acc) {
+  const long hn = __ldg(a.nbr + (long)d * a.Vh + h);
+  float psi[24];
+  load_narrow(a.in, hn, s, a.Lh, psi);
+  float u[18];
+  load_link(a.links + (h * 8 + d) * 18, u);
+  hop_dir<MU, SG>(psi, u, acc);
+}
+
+template <int DAG>
+__global__ void __launch_bounds__(256) hop_lp_kernel(const HopLPArgs a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ double red[32];
+  float* tile = reinterpret_cast<float*>(smraw);
+  const int Ls = a.Ls;
+  const int NS = a.NS;
+  const int i = threadIdx.x / Ls;
+  const int s = threadIdx.x - i * Ls;
+  const long h = (long)blockIdx.x * NS + i;
+  const bool act = (i < NS) && (h < a.Vh);
+  const long left = a.Vh - (long)blockIdx.x * NS;
+  const int nact = left < NS ? (int)left : NS;
+  float acc[24];
+#pragma unroll
+  for (int k = 0; k < 24; ++k) acc[k] = 0.f;
+  if (act) {
+    constexpr int F = DAG ? -1 : 1;
+    dir_lp<0, F>(a, h, s, 0, acc);
+    dir_lp<1, F>(a, h, s, 1, acc);
+    dir_lp<2, F>(a, h, s, 2, acc);
+    dir_lp<3, F>(a, h, s, 3, acc);
+    dir_lp<0, -F>(a, h, s, 4, acc);
+    dir_lp<1, -F>(a, h, s, 5, acc);
+    dir_lp<2, -F>(a, h, s, 6, acc);
+    dir_lp<3, -F>(a, h, s, 7, acc);
+  }
+#pragma unroll
+  for (int k = 0; k < 24; ++k) acc[k] *= a.scale;
+  if (a.x != nullptr) {
+    float xv[24];
+    if (act) load_narrow(a.x, h, s, a.Lh, xv);
+    if (a.ex.kind != 0) sop_apply(a.ex, xv, tile, i, s, act, nact, Ls);
+#pragma unroll
+    for (int k = 0; k < 24; ++k) acc[k] = fmaf(a.xscale, xv[k], acc[k]);
+  }
+  if (a.eout.kind != 0) sop_apply(a.eout, acc, tile, i, s, act, nact, Ls);
+  double part = 0.0;
+  if (act) {
+    double* base = a.out + elem_index(h, 0, s >> 1, a.Lh) + (s & 1);
+    float ps = 0.f;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      base[(long)k * a.Lh * 4] = widen_bits(acc[2 * k]);
+      base[(long)k * a.Lh * 4 + 2] = widen_bits(acc[2 * k + 1]);
+      ps = fmaf(acc[2 * k], acc[2 * k], fmaf(acc[2 * k + 1], acc[2 * k + 1], ps));
+    }
+    part = (double)ps;
+  }
+  if (a.partials) {
+    const double t = block_sum<256>(part, red);
+    if (threadIdx.x == 0) a.partials[blockIdx.x] = t;
+  }
+}
+
 // ---------------------------------------------------------------- s-local kernel
 
 template <class S> struct SopArgs {
@@ -229,7 +349,34 @@ static dwf_status hop_t(dwf_lattice* L, const HopCall& c) {
   if (L->timing) DWF_TRY(timing_begin(L, &ta, &tb));
   int NS2 = 0;
   if constexpr (sizeof(S) <= 4) NS2 = hop2_sites(L->Ls, pi, 1);
-  if (NS2 > 0) {
+  const bool lp = sizeof(S) == 8 && (L->fp64_in_fp32 > 0 || L->fp64_arith == 1);
+  if (lp) {
+    HopLPArgs b;
+    b.in = reinterpret_cast<const double*>(c.in.v);
+    b.out = reinterpret_cast<double*>(c.out.v);
+    b.x = c.has_x ? reinterpret_cast<const double*>(c.x.v) : nullptr;
+    b.links = reinterpret_cast<const float*>(L->links[DWF_F32][c.out_parity]);
+    b.nbr = L->nbr[c.out_parity];
+    b.Vh = L->Vh;
+    b.Ls = L->Ls;
+    b.Lh = L->Lh;
+    b.NS = NS;
+    b.ex = sop_k<float>(c.has_x ? c.ops : nullptr, c.ex, L->Ls);
+    b.eout = sop_k<float>(c.ops, c.eout, L->Ls);
+    b.scale = (float)c.scale;
+    b.xscale = (float)c.xscale;
+    b.partials = c.partials;
+    const size_t smem32 = (b.ex.kind || b.eout.kind) ? tile_bytes<float>(NS, L->Ls) : 0;
+    if (c.dag) {
+      if (smem32 > 48 * 1024)
+        DWF_CUDA(L, cudaFuncSetAttribute(hop_lp_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem32));
+      hop_lp_kernel<1><<<(unsigned)blocks, threads, smem32, L->stream>>>(b);
+    } else {
+      if (smem32 > 48 * 1024)
+        DWF_CUDA(L, cudaFuncSetAttribute(hop_lp_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem32));
+      hop_lp_kernel<0><<<(unsigned)blocks, threads, smem32, L->stream>>>(b);
+    }
+  } else if (NS2 > 0) {
     if constexpr (sizeof(S) <= 4) {
       HopBatch b;
       b.nrhs = 1;

@@ -649,6 +649,13 @@ dwf_status dwf_set_wait_limit(dwf_lattice_t L, long long polls) {
   return DWF_OK;
 }
 
+dwf_status dwf_set_fp64_arithmetic(dwf_lattice_t L, int mode) {
+  if (!L) return fail(L, DWF_ERR_INVALID_ARG, "dwf_set_fp64_arithmetic: null handle");
+  if (mode != 0 && mode != 1) return fail(L, DWF_ERR_INVALID_ARG, "dwf_set_fp64_arithmetic: mode must be 0 or 1");
+  L->fp64_arith = mode;
+  return DWF_OK;
+}
+
 dwf_status dwf_get_launch_count(dwf_lattice_t L, long long* launches) {
   if (!L || !launches) return fail(L, DWF_ERR_INVALID_ARG, "dwf_get_launch_count: null argument");
   *launches = L->launches;

@@ -194,6 +194,11 @@ extern "C" dwf_status madwf_solve(dwf_lattice_t L, dwf_lattice_t Li, double m, c
   dwf_cg_params mob{prm->tol_mob, prm->max_iter, prm->inner, inter_delta(prm->tol_mob), prm->check_every};
   dwf_cg_params fin{prm->tol_final, prm->max_iter, prm->inner, prm->delta, prm->check_every};
 
+  // FP32 arithmetic for the passes' FP64-field hops (see below) where its
+  // residual floor, ~1e-7 times the operator's condition number, stays well
+  // under the tolerances: the Pauli-Villars operator (mass 1) is well
+  // conditioned; the Moebius one at the light mass much less so
+  const bool pass_fp32 = prm->inner != DWF_F64 && prm->tol_pv >= 1e-5 && prm->tol_mob >= 1e-4;
   dwf_status status = DWF_OK;
   if (bnorm > 0.0) {
     for (int pass = 0; pass < prm->n_dc; ++pass) {
@@ -210,41 +215,48 @@ extern "C" dwf_status madwf_solve(dwf_lattice_t L, dwf_lattice_t Li, double m, c
       }
       if (pass > 0) st.pass_resid[pass - 1] = rn / bnorm;
       if (rn <= prm->tol_final * bnorm) break;
-      // 1. c = P^-1 D(1)^-1 r
-      DWF_TRY(timed_solve(L, 1.0, re, ro, te, to, pv, &st.pv));
-      DWF_TRY(pshift(L, te, ce, -1));
-      DWF_TRY(pshift(L, to, co, -1));
-      // 2-3. c' = (c_1, 0, ...) on the Moebius lattice; D'(m) z = D'(1) P c'
-      DWF_TRY(slice(Li, qe, 0, L, ce, 0, 1.0, true));
-      DWF_TRY(slice(Li, qo, 0, L, co, 0, 1.0, true));
-      DWF_TRY(pshift(Li, qe, pe, +1));
-      DWF_TRY(pshift(Li, qo, po, +1));
-      DWF_TRY(apply_D(Li, ops1_in, false, pe, po, qe, qo));
       {
-        dwf_status s = timed_solve(Li, m, qe, qo, ze, zo, mob, &st.mobius);
-        if (s != DWF_OK) return fail(L, s, "madwf_solve (Moebius solve): " + Li->err);
+        // The pass's solves and the operator applications that make their
+        // sources need only their own loose tolerances, so (pass_fp32) their
+        // FP64-field hops compute in FP32: GB300 runs FP64 at ~1/70 of its
+        // FP32 rate.  The residuals b - D x between passes stay FP64.
+        Fp32StepScope lp_outer(L, pass_fp32), lp_inner(Li, pass_fp32);
+        // 1. c = P^-1 D(1)^-1 r
+        DWF_TRY(timed_solve(L, 1.0, re, ro, te, to, pv, &st.pv));
+        DWF_TRY(pshift(L, te, ce, -1));
+        DWF_TRY(pshift(L, to, co, -1));
+        // 2-3. c' = (c_1, 0, ...) on the Moebius lattice; D'(m) z = D'(1) P c'
+        DWF_TRY(slice(Li, qe, 0, L, ce, 0, 1.0, true));
+        DWF_TRY(slice(Li, qo, 0, L, co, 0, 1.0, true));
+        DWF_TRY(pshift(Li, qe, pe, +1));
+        DWF_TRY(pshift(Li, qo, po, +1));
+        DWF_TRY(apply_D(Li, ops1_in, false, pe, po, qe, qo));
+        {
+          dwf_status s = timed_solve(Li, m, qe, qo, ze, zo, mob, &st.mobius);
+          if (s != DWF_OK) return fail(L, s, "madwf_solve (Moebius solve): " + Li->err);
+        }
+        // y'_1 = (P^-1 z)_1
+        DWF_TRY(pshift(Li, ze, pe, -1));
+        DWF_TRY(pshift(Li, zo, po, -1));
+        // 4. w = (-y'_1, c_2, ..., c_L); u = P^-1 D(1)^-1 D(m) P w
+        DWF_TRY(blas_copy(L, ce, ue));
+        DWF_TRY(blas_copy(L, co, uo));
+        DWF_TRY(slice(L, ue, 0, Li, pe, 0, -1.0, false));
+        DWF_TRY(slice(L, uo, 0, Li, po, 0, -1.0, false));
+        DWF_TRY(pshift(L, ue, ye, +1));
+        DWF_TRY(pshift(L, uo, yo, +1));
+        DWF_TRY(apply_D(L, ops_m, false, ye, yo, re, ro));
+        DWF_TRY(timed_solve(L, 1.0, re, ro, te, to, pv, &st.pv));
+        DWF_TRY(pshift(L, te, ue, -1));
+        DWF_TRY(pshift(L, to, uo, -1));
+        // y' = (y'_1, u_2, ..., u_L); x += P y'
+        DWF_TRY(slice(L, ue, 0, Li, pe, 0, 1.0, false));
+        DWF_TRY(slice(L, uo, 0, Li, po, 0, 1.0, false));
+        DWF_TRY(pshift(L, ue, ye, +1));
+        DWF_TRY(pshift(L, uo, yo, +1));
+        DWF_TRY(blas_axpby(L, 1.0, ye, 1.0, xe));
+        DWF_TRY(blas_axpby(L, 1.0, yo, 1.0, xo));
       }
-      // y'_1 = (P^-1 z)_1
-      DWF_TRY(pshift(Li, ze, pe, -1));
-      DWF_TRY(pshift(Li, zo, po, -1));
-      // 4. w = (-y'_1, c_2, ..., c_L); u = P^-1 D(1)^-1 D(m) P w
-      DWF_TRY(blas_copy(L, ce, ue));
-      DWF_TRY(blas_copy(L, co, uo));
-      DWF_TRY(slice(L, ue, 0, Li, pe, 0, -1.0, false));
-      DWF_TRY(slice(L, uo, 0, Li, po, 0, -1.0, false));
-      DWF_TRY(pshift(L, ue, ye, +1));
-      DWF_TRY(pshift(L, uo, yo, +1));
-      DWF_TRY(apply_D(L, ops_m, false, ye, yo, re, ro));
-      DWF_TRY(timed_solve(L, 1.0, re, ro, te, to, pv, &st.pv));
-      DWF_TRY(pshift(L, te, ue, -1));
-      DWF_TRY(pshift(L, to, uo, -1));
-      // y' = (y'_1, u_2, ..., u_L); x += P y'
-      DWF_TRY(slice(L, ue, 0, Li, pe, 0, 1.0, false));
-      DWF_TRY(slice(L, uo, 0, Li, po, 0, 1.0, false));
-      DWF_TRY(pshift(L, ue, ye, +1));
-      DWF_TRY(pshift(L, uo, yo, +1));
-      DWF_TRY(blas_axpby(L, 1.0, ye, 1.0, xe));
-      DWF_TRY(blas_axpby(L, 1.0, yo, 1.0, xo));
       ++st.passes;
     }
     if (st.passes > 0) {

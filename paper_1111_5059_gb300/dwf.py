@@ -125,6 +125,7 @@ def _declare(lib):
         "dwf_get_launch_count": [H, ctypes.POINTER(ctypes.c_longlong)],
         "dwf_apply_Mpc_prec": [H, ctypes.c_double, ctypes.c_int, ctypes.c_int, _VP, _VP],
         "dwf_set_wait_limit": [H, ctypes.c_longlong],
+        "dwf_set_fp64_arithmetic": [H, ctypes.c_int],
         "dwf_md_trajectory": [H, ctypes.c_int, ctypes.POINTER(Quotient), ctypes.POINTER(_VP), _VP, _VP,
                               ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(CGParams),
                               ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
@@ -291,6 +292,11 @@ class Lattice:
         """Polls of the hop kernel's bounded consumer waits on later launches
         (-1: the default; 0: every wait gives up at once)."""
         self._call(lib().dwf_set_wait_limit, int(polls))
+
+    def set_fp64_arithmetic(self, mode: int = 0):
+        """Arithmetic of the hops on FP64 fields (include/dwf.h,
+        dwf_set_fp64_arithmetic): 0 FP64, 1 FP32."""
+        self._call(lib().dwf_set_fp64_arithmetic, int(mode))
 
     def apply_Mpc_noalloc(self, m: float, x: torch.Tensor, out: torch.Tensor, dag: bool = False) -> torch.Tensor:
         """apply_Mpc into a caller-provided `out`; the library allocates no

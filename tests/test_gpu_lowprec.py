@@ -15,6 +15,9 @@ Tolerances (max |gpu - oracle| over max |oracle|), derived from the storage:
     FP16 as well; the errors of independent roundings add in quadrature over
     the terms of an output element.  Bar: 2e-3.
   * FP64: the FP64 path through the same entry point, 1e-13 (as dwf_apply_Mpc).
+  * FP64 fields in FP32 arithmetic (dwf_set_fp64_arithmetic(1), the
+    arithmetic of the MADWF passes' loose solves): inputs truncated to FP32
+    (relative error below 2^-23) and FP32 links; the FP32 bar, 1e-5.
 
 Shapes: the bench's fifth-dimension extents (Ls = 12 Moebius, 16 and 32
 Shamir) on lattices of several site groups with a ragged tail, the
@@ -36,7 +39,7 @@ from paper_1111_5059_gb300 import inputs as I
 pytestmark = pytest.mark.gpu
 
 M5 = 1.8
-TOL = {"f64": 1e-13, "f32": 1e-5, "f16": 2e-3}
+TOL = {"f64": 1e-13, "f32": 1e-5, "f16": 2e-3, "f64-in-f32": 1e-5}
 
 CASES = [
     # dims (X,Y,Z,T), Ls, b, c, bc_t, m
@@ -104,3 +107,18 @@ def test_timed_out_wait_reports_and_handle_stays_usable(dwf):
     assert torch.equal(again, ref)
     torch.cuda.synchronize()
     lat.close()
+
+
+@pytest.mark.parametrize("dag", [False, True])
+def test_Mpc_on_fp64_fields_in_fp32_arithmetic(case, dag):
+    lat, psi, m, want, eo = case
+    lat.set_fp64_arithmetic(1)
+    try:
+        got = lat.apply_Mpc_prec(m, _to(psi), prec="f64", dag=dag).cpu().numpy()
+    finally:
+        lat.set_fp64_arithmetic(0)
+    err = _rel(got, want[dag])
+    assert err < TOL["f64-in-f32"], err
+    assert err > 1e-12  # the FP32 path did run
+    back = lat.apply_Mpc_prec(m, _to(psi), prec="f64", dag=dag).cpu().numpy()
+    assert _rel(back, want[dag]) < TOL["f64"]  # and mode 0 restores FP64

@@ -92,6 +92,34 @@ def test_madwf_mixed_reaches_1e10(dwf, prec):
     inner.close()
 
 
+@pytest.mark.parametrize("n_dc,tol_pv,tol_mob", [(1, 1e-3, 1e-2), (2, 1e-4, 1e-3)])
+def test_madwf_fp32_passes(dwf, n_dc, tol_pv, tol_mob):
+    """Loose intermediate tolerances (the benchmark's settings, and two
+    passes): the passes' FP64-field hops compute in FP32.  Pass residuals as
+    the oracle's MADWF with the same tolerances (its solves in FP64), and the
+    final solve reaches 1e-10 by the oracle's operator."""
+    dims, Ls, Lp, m = (4, 4, 4, 8), 16, 6, 0.01
+    al = Ls / Lp
+    b5, c5 = (al + 1) / 2, (al - 1) / 2
+    U = I.gauge_field(3, dims, 0.5)
+    src = I.gaussian_spinor(3, dims, Ls)
+    outer, inner = _pair(dwf, dims, Ls, Lp, b5, c5, U)
+    r = dwf.madwf_solve(outer, inner, m, _to(src), n_dc=n_dc, tol_pv=tol_pv, tol_mob=tol_mob, tol_final=1e-10,
+                        inner_prec="f32", delta=1e-3, check_every=1)
+    st = r.stats
+    _, info = O.madwf(U, src, m, M5, Lp, b5, c5, n_dc=n_dc, tol_pv=tol_pv, tol_mob=tol_mob, tol_final=1e-10)
+    assert st["passes"] == n_dc
+    for got, want in zip(st["pass_resid"][:n_dc], info["passes"]):
+        # both are |b - D x| / |b| after inexact inner solves: equal up to
+        # those solves' tolerances, not to rounding
+        assert 0.5 * want < got < 2.0 * want, (got, want)
+    x = r.x.cpu().numpy()
+    res = np.sqrt(O.norm2(src - O.dwf_op(U, x, m, M5)) / O.norm2(src))
+    assert res <= 1e-10
+    outer.close()
+    inner.close()
+
+
 def test_madwf_rejects_mismatched_lattices(dwf):
     U = I.gauge_field(1, (4, 4, 4, 4), 0.3)
     outer = dwf.Lattice((4, 4, 4, 4), 8, M5)

@@ -16,7 +16,8 @@ A step is one solve from a zero guess on seeded synthetic inputs already
 resident in HBM (timed with CUDA events on the solve's stream).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload madwf|mixed|hopprof|ladder]
-                  [--impl native|reference] [--study] [--md-study] [--no-fp64] [--no-extras]
+                  [--impl native|reference] [--study] [--md-study] [--hasenbusch-study] [--no-fp64]
+                  [--no-extras]
                   [--no-cpu-baseline]
 
 --study (with the madwf workload) sweeps the MADWF settings (defect-correction
@@ -123,6 +124,8 @@ def parse():
     ap.add_argument("--inner", default=None, choices=["f32", "f16"], help="inner precision (default per workload)")
     ap.add_argument("--study", action="store_true", help="sweep the MADWF settings (madwf workload)")
     ap.add_argument("--md-study", action="store_true", help="FGI against Omelyan trajectories on the force workload")
+    ap.add_argument("--hasenbusch-study", action="store_true",
+                    help="geometric and force-balanced Hasenbusch ladders, force solves at 1e-8 and 1e-6")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 CG comparison solve")
     ap.add_argument("--no-extras", action="store_true", help="skip the precision comparison and the ladder")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -885,13 +888,82 @@ def run_md_study(args, dev):
             e0, e1 = _events(2)
             e0.record(stream)
             H0, H1, st, nf = dwf.md_trajectory(lat, terms, phis, U, p, length / n, n, integrator=integ, tol=1e-10,
-                                               inner="f32", delta=DELTA)
+                                               inner="f32", delta=1e-2)
             e1.record(stream)
             e1.synchronize()
             print(json.dumps({"study": "md", "workload": "force-shamir-16^3x8-Ls16-2terms", "integrator": integ,
                               "tau": length / n, "nsteps": n, "length": length, "dH": H1 - H0, "H0": H0,
                               "force_evaluations": nf, "cg_iters": st["iters"],
                               "seconds": e0.elapsed_time(e1) / 1e3}), flush=True)
+    lat.close()
+
+
+def run_hasenbusch_study(args, dev):
+    """Hasenbusch ladder tuning (Sec. 3) on the force workload (Shamir
+    16^3 x 8 x Ls=16, m = 0.01, Pauli-Villars mass 1, eps = 0.5, seed 4): for
+    k = 0..3 intermediate masses, the geometric ladder and the ladder tuned to
+    equal per-term force norms (paper_1111_5059_gb300.hasenbusch.tune_ladder);
+    each term's pseudofermion from the heat bath (Gaussian eta, seed 60 + i).
+    Per ladder: the terms' force norms (RMS and max over links of |F_mu(n)|)
+    and CG iterations at force-solve tolerances 1e-8 and 1e-6, then one FGI
+    trajectory (tau = 0.1, 4 steps) at each tolerance from the same momenta
+    (seed 4): dH, the reversibility error max |U - U0| after the trajectory
+    and its reverse, CG iterations and time.  One JSON line per ladder."""
+    import torch
+
+    from paper_1111_5059_gb300 import dwf, hasenbusch, inputs
+
+    dims, Ls, M5, m = (16, 16, 16, 8), 16, 1.8, 0.01
+    stream = torch.cuda.current_stream(dev)
+    U0 = torch.from_numpy(inputs.gauge_field(4, dims, 0.5)).to(dev)
+    p0 = torch.from_numpy(inputs.gaussian_momenta(4, dims)).to(dev)
+    etas = [torch.from_numpy(inputs.gaussian_spinor(60 + i, dims, Ls)).to(dev) for i in range(4)]
+    lat = dwf.Lattice(dims, Ls, M5, 1.0, 0.0, 1, stream=stream, device=dev)
+    lat.set_gauge(U0)
+
+    def phis_of(ts):
+        return [dwf.heatbath(lat, t, etas[i], tol=1e-10, inner="f32", delta=DELTA)[0] for i, t in enumerate(ts)]
+
+    def term_data(ts, tol):
+        phis = phis_of(ts)
+        out = []
+        for t, ph in zip(ts, phis):
+            _, F, _, st = dwf.force(lat, [t], [ph], tol=tol, inner="f32", delta=DELTA)
+            n2 = (F * F).sum(dim=-1)  # |F_mu(n)|^2
+            out.append({"rms": float(n2.mean().sqrt()), "max": float(n2.max().sqrt()), "iters": st["iters"]})
+        return out
+
+    cases = [("geometric", 0), ("geometric", 1)] + [("tuned", k) for k in (1, 2, 3)]
+    for kind, k in cases:
+        ladder = hasenbusch.geometric_ladder(m, k)
+        tune_iters = 0
+        if kind == "tuned":
+            ladder, hist = hasenbusch.tune_ladder(
+                ladder, lambda ts: [d["rms"] for d in term_data(ts, 1e-8)], iters=8, rtol=0.05)
+            tune_iters = len(hist)
+        ts = hasenbusch.terms(ladder)
+        d8, d6 = term_data(ts, 1e-8), term_data(ts, 1e-6)
+        phis = phis_of(ts)
+        traj = {}
+        for tol in (1e-8, 1e-6):
+            U, p = U0.clone(), p0.clone()
+            e0, e1 = _events(2)
+            e0.record(stream)
+            H0, H1, st, nf = dwf.md_trajectory(lat, ts, phis, U, p, 0.1, 4, integrator="fgi", tol=tol, inner="f32",
+                                               delta=DELTA)
+            e1.record(stream)
+            e1.synchronize()
+            secs = e0.elapsed_time(e1) / 1e3
+            p.neg_()
+            dwf.md_trajectory(lat, ts, phis, U, p, 0.1, 4, integrator="fgi", tol=tol, inner="f32", delta=DELTA)
+            traj[f"{tol:.0e}"] = {"dH": H1 - H0, "H0": H0, "reversibility_max_dU": float((U - U0).abs().max()),
+                                  "force_evaluations": nf, "cg_iters": st["iters"], "seconds": secs}
+            lat.set_gauge(U0)
+        print(json.dumps({"study": "hasenbusch", "workload": "force-shamir-16^3x8-Ls16", "m": m, "ladder": kind,
+                          "k": k, "masses": ladder, "tune_evaluations": tune_iters,
+                          "term_force_rms": [d["rms"] for d in d8], "term_force_max": [d["max"] for d in d8],
+                          "term_iters_1e-8": [d["iters"] for d in d8], "term_iters_1e-6": [d["iters"] for d in d6],
+                          "trajectory": traj}), flush=True)
     lat.close()
 
 
@@ -916,6 +988,9 @@ def main():
     hbm_peak, peak_src = measured_peak()
     if args.md_study:
         run_md_study(args, dev)
+        return
+    if args.hasenbusch_study:
+        run_hasenbusch_study(args, dev)
         return
     if args.study:
         if not w["madwf"]:

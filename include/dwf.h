@@ -221,6 +221,16 @@ typedef struct {
 dwf_status dwf_force(dwf_lattice_t h, int nterms, const dwf_quotient* terms, const void* const* phi,
                      void* const* X_io, void* F, void* G, double* S, const dwf_cg_params* cg, dwf_stats* stats);
 
+/* Heat-bath pseudofermion of one quotient term (Sec. 3): given eta (device
+ * whole-lattice spinor, even sites used; Gaussian in an HMC trajectory's
+ * refresh), phi = M2^-+ M1^+ eta (device whole-lattice spinor, written on
+ * even sites, odd sites zero), so that the term's action at this gauge field
+ * is S = |M1^-+ M2^+ phi|^2 = |eta_e|^2.  One CG solve with M2 on the normal
+ * equations (parameters `cg`; stats may be NULL).  eta and phi must not
+ * alias. */
+dwf_status dwf_heatbath(dwf_lattice_t h, dwf_quotient term, const void* eta, void* phi, const dwf_cg_params* cg,
+                        dwf_stats* stats);
+
 /* The action alone: S (host double, required) = sum over the terms of
  * |M1 (M1^+ M1)^-1 M2^+ phi|^2, as dwf_force computes it with F = G = NULL. */
 dwf_status dwf_action(dwf_lattice_t h, int nterms, const dwf_quotient* terms, const void* const* phi,

@@ -484,6 +484,52 @@ dwf_status dwf_force(dwf_lattice_t L, int nterms, const dwf_quotient* terms, con
   return DWF_OK;
 }
 
+dwf_status dwf_heatbath(dwf_lattice_t L, dwf_quotient term, const void* eta, void* phi, const dwf_cg_params* prm,
+                        dwf_stats* stats) {
+  if (!L || !eta || !phi || !prm) return fail(L, DWF_ERR_INVALID_ARG, "dwf_heatbath: null argument");
+  if (eta == phi) return fail(L, DWF_ERR_INVALID_ARG, "dwf_heatbath: eta and phi must not alias");
+  if (!std::isfinite(term.m1) || !std::isfinite(term.m2))
+    return fail(L, DWF_ERR_INVALID_ARG, "dwf_heatbath: non-finite mass");
+  if (!L->gauge_set) return fail(L, DWF_ERR_INVALID_ARG, "dwf_heatbath: gauge field not set");
+  auto t0 = std::chrono::steady_clock::now();
+  const long long l0 = L->launches;
+  dwf_status s0;
+  const SOps* o1 = sops_for(L, term.m1, &s0);
+  if (!o1) return s0;
+  const SOps* o2 = sops_for(L, term.m2, &s0);
+  if (!o2) return s0;
+  Field ee, w, v, xt, X, Y;
+  DWF_TRY(field_alloc(L, "hb.eta", DWF_F64, &ee));
+  DWF_TRY(field_alloc(L, "hb.w", DWF_F64, &w));
+  DWF_TRY(field_alloc(L, "hb.v", DWF_F64, &v));
+  DWF_TRY(field_alloc(L, "hb.xt", DWF_F64, &xt));
+  DWF_TRY(field_alloc(L, "hb.X", DWF_F64, &X));
+  DWF_TRY(field_alloc(L, "hb.Y", DWF_F64, &Y));
+  long long hops = 0;
+  // phi = M2^-+ M1^+ eta = M2 (M2^+ M2)^-1 M1^+ eta: then M1^-+ M2^+ phi = eta
+  // and the quotient's action is |eta|^2
+  DWF_TRY(launch_pack(L, eta, 0, ee));
+  DWF_TRY(apply_Mpc_internal(L, o1, true, ee, w));
+  hops += 2;
+  // (M2^+ M2) X = w with M2 = M~ B: (M~^+ M~) x~ = B^-+ w, X = B^-1 x~
+  DWF_TRY(launch_sop(L, w, v, o2, SOps::BINVT, 1.0, nullptr, 0.0));
+  DWF_TRY(blas_zero(L, xt));
+  dwf_stats st{};
+  DWF_TRY(cgne_core(L, o2, v, xt, *prm, &st, &hops));
+  DWF_TRY(launch_sop(L, xt, X, o2, SOps::BINV, 1.0, nullptr, 0.0));
+  DWF_TRY(apply_Mpc_internal(L, o2, false, X, Y));
+  hops += 2;
+  DWF_TRY(launch_unpack(L, Y, 0, phi, true));
+  DWF_CUDA(L, cudaStreamSynchronize(L->stream));
+  DWF_TRY(check_dev_err(L));
+  st.hop_calls = hops;
+  st.op_count = (long long)st.iters * L->Ls;
+  st.launches = L->launches - l0;
+  st.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (stats) *stats = st;
+  return DWF_OK;
+}
+
 dwf_status fgi_link_update(dwf_lattice_t L, const void* Xc, double coeff, const void* U_in, void* U_out) {
   if (!L || !Xc || !U_in || !U_out || !std::isfinite(coeff))
     return fail(L, DWF_ERR_INVALID_ARG, "fgi_link_update: bad argument");

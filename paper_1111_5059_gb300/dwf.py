@@ -125,6 +125,7 @@ def _declare(lib):
         "dwf_get_launch_count": [H, ctypes.POINTER(ctypes.c_longlong)],
         "dwf_apply_Mpc_prec": [H, ctypes.c_double, ctypes.c_int, ctypes.c_int, _VP, _VP],
         "dwf_set_wait_limit": [H, ctypes.c_longlong],
+        "dwf_heatbath": [H, Quotient, _VP, _VP, ctypes.POINTER(CGParams), ctypes.POINTER(Stats)],
         "dwf_set_fp64_arithmetic": [H, ctypes.c_int],
         "dwf_md_trajectory": [H, ctypes.c_int, ctypes.POINTER(Quotient), ctypes.POINTER(_VP), _VP, _VP,
                               ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(CGParams),
@@ -441,6 +442,18 @@ def fgi_step(lat: Lattice, terms, phis, U: torch.Tensor, p: torch.Tensor, tau: f
               _VP(_ptr(U, lat.gauge_shape)), _VP(_ptr(p, dtype=torch.float64)), float(tau), int(bool(forecast)),
               ctypes.byref(prm), ctypes.byref(st), fg)
     return st.as_dict(), (fg[0], fg[1])
+
+
+def heatbath(lat: Lattice, term, eta: torch.Tensor, tol=1e-12, inner="f64", max_iter=100000, delta=0.1):
+    """phi = M2^-+ M1^+ eta for the quotient term (m1, m2) (see include/dwf.h,
+    dwf_heatbath): the term's action at this gauge field is |eta_e|^2.
+    Returns (phi, stats)."""
+    phi = torch.empty_like(eta)
+    st = Stats()
+    prm = CGParams(float(tol), int(max_iter), _PREC[inner], float(delta), 10)
+    lat._call(lib().dwf_heatbath, Quotient(float(term[0]), float(term[1])), _VP(_ptr(eta, lat.spinor_shape)),
+              _VP(_ptr(phi, lat.spinor_shape)), ctypes.byref(prm), ctypes.byref(st))
+    return phi, st.as_dict()
 
 
 INTEGRATORS = {"fgi": 0, "omelyan": 1}

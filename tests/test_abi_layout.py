@@ -147,6 +147,8 @@ def test_null_handle_is_rejected_by_every_entry_point(lib):
         ("dwf_get_launch_count", lambda: L.dwf_get_launch_count(None, None), "dwf_get_launch_count:"),
         ("dwf_apply_Mpc_prec", lambda: L.dwf_apply_Mpc_prec(None, 0.1, 0, 1, None, None), "dwf_apply_Mpc_prec:"),
         ("dwf_set_wait_limit", lambda: L.dwf_set_wait_limit(None, 0), "dwf_set_wait_limit:"),
+        ("dwf_heatbath", lambda: L.dwf_heatbath(None, dwf.Quotient(0.1, 1.0), None, None, None, None),
+         "dwf_heatbath:"),
         ("dwf_set_fp64_arithmetic", lambda: L.dwf_set_fp64_arithmetic(None, 1), "dwf_set_fp64_arithmetic:"),
         ("dwf_md_trajectory", lambda: L.dwf_md_trajectory(None, 1, None, None, None, None, 0.1, 1, 0, 1, None, None,
                                                           None, None, None), "dwf_md_trajectory:"),

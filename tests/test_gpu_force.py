@@ -188,3 +188,69 @@ def test_force_workload_size_properties(dwf):
     assert (U1 - Ut).abs().max().item() < 1e-8
     assert (p1 + _to(p)).abs().max().item() < 1e-7
     lat.close()
+
+
+def test_heatbath_matches_oracle(small, dwf):
+    """phi = M2^-+ M1^+ eta (dwf_heatbath) element by element against the
+    oracle's heat bath, and the term's action at that field is |eta_e|^2."""
+    lat, U, phis, _ = small
+    dims, Ls = lat.dims, lat.Ls
+    eta = I.gaussian_spinor(71, dims, Ls)
+    for m1, m2 in TERMS:
+        phi, st = dwf.heatbath(lat, (m1, m2), _to(eta), tol=1e-13)
+        want = O.heatbath_phi(U, eta, m1, m2, M5, tol=1e-14)
+        got = phi.cpu().numpy()
+        assert np.abs(got - want).max() <= 1e-10 * np.abs(want).max()
+        assert st["iters"] > 0
+        ee = eta * O.EO(U, m1, M5, Ls).even
+        S = dwf.action_value(lat, [(m1, m2)], [phi], tol=1e-13)
+        assert abs(S - O.norm2(ee)) <= 1e-10 * O.norm2(ee)
+
+
+def test_heatbath_at_force_workload_size(dwf):
+    """16^3 x 8 x Ls=16, terms (0.01, 0.1) and (0.1, 1): S(phi) = |eta_e|^2."""
+    dims, Ls = (16, 16, 16, 8), 16
+    U = I.gauge_field(4, dims, 0.5)
+    lat = dwf.Lattice(dims, Ls, M5)
+    lat.set_gauge(_to(U))
+    eta = _to(I.gaussian_spinor(72, dims, Ls))
+    for term in ((0.01, 0.1), (0.1, 1.0)):
+        phi, _ = dwf.heatbath(lat, term, eta, tol=1e-12)
+        S = dwf.action_value(lat, [term], [phi], tol=1e-12)
+        e2 = float((eta.abs() ** 2 * _even_mask(dims, Ls)).sum())
+        assert abs(S - e2) <= 1e-9 * e2, (S, e2)
+    lat.close()
+
+
+def _even_mask(dims, Ls):
+    X, Y, Z, T = dims
+    t, z, y, x = np.meshgrid(np.arange(T), np.arange(Z), np.arange(Y), np.arange(X), indexing="ij")
+    m = ((x + y + z + t) % 2 == 0).astype(np.float64)
+    return torch.from_numpy(np.broadcast_to(m[None, :, :, :, :, None, None], (Ls, T, Z, Y, X, 4, 3)).copy()).cuda()
+
+
+def test_hasenbusch_ladder_tuning_balances_gpu_forces(dwf):
+    """The tuning loop of the Hasenbusch ladder (Sec. 3) driven by GPU force
+    norms of heat-bath pseudofermions: the tuned terms' RMS forces agree to
+    10 %, the end masses stay put and the ladder stays ordered."""
+    from paper_1111_5059_gb300 import hasenbusch as Hb
+
+    dims, Ls, m = (4, 4, 4, 8), 8, 0.02
+    lat = dwf.Lattice(dims, Ls, M5)
+    lat.set_gauge(_to(I.gauge_field(9, dims, 0.5)))
+    etas = [_to(I.gaussian_spinor(90 + i, dims, Ls)) for i in range(3)]
+
+    def norms(ts):
+        out = []
+        for i, t in enumerate(ts):
+            phi, _ = dwf.heatbath(lat, t, etas[i], tol=1e-11)
+            _, F, _, _ = dwf.force(lat, [t], [phi], tol=1e-10)
+            out.append(float((F * F).sum(dim=-1).mean().sqrt()))
+        return out
+
+    start = Hb.geometric_ladder(m, 2)
+    ms, hist = Hb.tune_ladder(start, norms, iters=10, rtol=0.1)
+    f = hist[-1][1]
+    assert max(f) / min(f) < 1.1, hist
+    assert ms[0] == m and ms[-1] == 1.0 and ms[0] < ms[1] < ms[2] < ms[3]
+    lat.close()

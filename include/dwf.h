@@ -188,7 +188,8 @@ typedef struct {
   dwf_stats mobius;    /* the n_dc Moebius solves (op_count in units of Ls') */
   dwf_stats final_cg;  /* the final warm-started DWF solve */
   int passes;          /* defect-correction passes done */
-  double pass_resid[MADWF_MAX_PASSES]; /* |b - D x| / |b| after each pass */
+  double pass_resid[MADWF_MAX_PASSES]; /* |b - D x| / |b| after each pass (the last one in FP32
+                                          arithmetic when the passes use it and it is >= 1e-5) */
 } madwf_stats;
 
 dwf_status madwf_solve(dwf_lattice_t outer, dwf_lattice_t inner, double m, const void* b, void* x,

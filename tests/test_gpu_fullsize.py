@@ -19,6 +19,10 @@ oracle,
     residual norm over them must be <= 1e-10 |b| (a necessary condition of
     the claimed total, and, the residual being spread over the lattice, the
     slabs' share of it is about sqrt(8/64) of the total).
+
+The operators the headline solve applies are also checked element by element
+at its full sizes: M_pc and M_pc^+ at 24^3 x 64 (Shamir Ls = 32, Moebius
+Ls' = 12) at sampled even sites, against the oracle on 6^4 patches.
 """
 import numpy as np
 import pytest
@@ -109,3 +113,37 @@ def test_madwf_24x64_Ls32_slab_oracle_residual(dwf, n_dc, tol_pv, tol_mob, delta
     # lattice their share of the library's reported total is ~sqrt(8/64); a
     # total under-reported by a large factor would fail this
     assert rel <= 4 * np.sqrt(8 / 64) * st["total"]["true_resid"] + 1e-14, (rel, st["total"]["true_resid"])
+
+
+@pytest.mark.parametrize("Ls,b5,c5", [(32, 1.0, 0.0), (12, 11 / 6, 5 / 6)])
+@pytest.mark.parametrize("prec,bar", [("f32", 1e-5), ("f64", 1e-13)])
+def test_Mpc_headline_size_sampled_sites(dwf, Ls, b5, c5, prec, bar):
+    """M_pc and M_pc^+ at the headline's sizes (24^3 x 64, the Shamir Ls = 32
+    outer and the Moebius Ls' = 12 inner operator, m = 0.002, eps = 0.6,
+    seed 3) through the solvers' own hop launches (dwf_apply_Mpc_prec),
+    element by element at 12 sampled even sites against the oracle on 6^4
+    patches around them (tests/oracle_residual.py, Mpc_at): FP32 storage to
+    1e-5 and FP64 to 1e-13 of the largest sampled |oracle| entry."""
+    dims, m = (24, 24, 24, 64), 0.002
+    U = I.gauge_field(3, dims, 0.6)
+    x = I.gaussian_spinor(3, dims, Ls)
+    lat = dwf.Lattice(dims, Ls, M5, b5, c5)
+    lat.set_gauge(torch.from_numpy(U).cuda())
+    xt = torch.from_numpy(x).cuda()
+    rng = np.random.default_rng(5)
+    sites = []
+    while len(sites) < 12:
+        c = tuple(int(rng.integers(0, L)) for L in dims)
+        if sum(c) % 2 == 0:
+            sites.append(c)
+    sites[0] = (0, 0, 0, 0)  # at the periodic corner
+    sites[1] = (23, 23, 23, 63)
+    for dag in (False, True):
+        y = lat.apply_Mpc_prec(m, xt, prec=prec, dag=dag)
+        got = [y[:, c[3], c[2], c[1], c[0]].cpu().numpy() for c in sites]
+        del y
+        want = [R.Mpc_at(U, x, m, M5, c, b5, c5, dag) for c in sites]
+        scale = max(np.abs(w).max() for w in want)
+        err = max(np.abs(g - w).max() for g, w in zip(got, want)) / scale
+        assert err < bar, (dag, err)
+    lat.close()

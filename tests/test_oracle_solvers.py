@@ -260,3 +260,59 @@ def test_dH_scales_as_tau4():
         dH.append(abs(O.hamiltonian(Uc, pc, phis, _TERMS, M5, tol=1e-13) - H0))
     ratio = dH[0] / dH[1]
     assert 12 < ratio < 20, (dH, ratio)
+
+
+def _even_subspace(eo, shape):
+    idx = np.flatnonzero(np.broadcast_to(eo.even, shape))
+
+    def embed(v):
+        full = np.zeros(int(np.prod(shape)), dtype=np.complex128)
+        full[idx] = v
+        return full.reshape(shape)
+
+    return idx, embed
+
+
+def test_quotient_action_is_the_determinant_ratio():
+    """Sec. 3: a quotient term (m1, m2) stands for det(M2^+ M2) / det(M1^+ M1).
+    The oracle's action S(phi) = |Y|^2 with Y = M1 X, X = (M1^+ M1)^-1 M2^+ phi
+    (quotient_solution) is the Gaussian form phi^+ W^+ W phi of the linear map
+    W : phi -> Y; integrating exp(-S) over phi gives det(W^+ W)^-1, so
+    |det W|^2 must equal |det M2|^2 / |det M1|^2, M = M_pc on the even
+    subspace (dense, from the oracle's operator).  A Hasenbusch ladder's terms
+    multiply to the ratio of its end masses (the telescoping of Sec. 3)."""
+    dims, Ls = (2, 2, 2, 2), 4
+    U = I.gauge_field(31, dims, 0.6)
+    shape = (Ls,) + tuple(reversed(dims)) + (4, 3)
+    eo_any = O.EO(U, 0.1, M5, Ls)
+    idx, embed = _even_subspace(eo_any, shape)
+    n = idx.size
+
+    def dense_M(m):
+        eo = O.EO(U, m, M5, Ls)
+        return np.stack([eo.Mpc(embed(np.eye(1, n, j, dtype=np.complex128)[0])).ravel()[idx] for j in range(n)], 1)
+
+    def logdet2_W(m1, m2):
+        M1 = dense_M(m1)
+        N1 = M1.conj().T @ M1
+
+        def solve_normal(eo, v):  # dense (M1^+ M1)^-1 on the even subspace
+            return embed(np.linalg.solve(N1, v.ravel()[idx]))
+
+        cols = []
+        for j in range(n):
+            phi = embed(np.eye(1, n, j, dtype=np.complex128)[0])
+            _, Y, _, _ = O.quotient_solution(U, phi, m1, m2, M5, dense=solve_normal)
+            cols.append(Y.ravel()[idx])
+        return 2 * np.linalg.slogdet(np.stack(cols, 1))[1]
+
+    def logdet2_M(m):
+        return 2 * np.linalg.slogdet(dense_M(m))[1]
+
+    ladder = [0.02, 0.2, 1.0]
+    terms = [logdet2_W(a, b) for a, b in zip(ladder, ladder[1:])]
+    for (a, b), t in zip(zip(ladder, ladder[1:]), terms):
+        assert t == pytest.approx(logdet2_M(b) - logdet2_M(a), abs=1e-8)
+    assert sum(terms) == pytest.approx(logdet2_M(1.0) - logdet2_M(0.02), abs=1e-8)
+    # a swapped term (M1 and M2 exchanged) would give the inverse ratio
+    assert abs(terms[0] - (logdet2_M(0.02) - logdet2_M(0.2))) > 1.0

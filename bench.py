@@ -125,6 +125,7 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--inner", default=None, choices=["f32", "f16"], help="inner precision (default per workload)")
     ap.add_argument("--study", action="store_true", help="sweep the MADWF settings (madwf workload)")
+    ap.add_argument("--study-ls", action="store_true", help="with --study: sweep Ls' and b + c in the bench's settings")
     ap.add_argument("--md-study", action="store_true", help="FGI against Omelyan trajectories on the force workload")
     ap.add_argument("--hasenbusch-study", action="store_true",
                     help="geometric and force-balanced Hasenbusch ladders, force solves at 1e-8 and 1e-6")
@@ -741,15 +742,48 @@ def run_madwf_study(args, w, dev):
     x = torch.empty_like(b)
     lat = dwf.Lattice(w["dims"], w["Ls"], w["M5"], 1.0, 0.0, 1, stream=stream, device=dev)
     lat.set_gauge(U)
-    Lp = w["inner_Ls"]
     mobs = {}
 
-    def mobius(alpha):
-        if alpha not in mobs:
+    def mobius(alpha, Lp=w["inner_Ls"]):
+        if (alpha, Lp) not in mobs:
             b5, c5 = (alpha + 1) / 2, (alpha - 1) / 2  # b - c = 1, b + c = alpha
-            mobs[alpha] = dwf.Lattice(w["dims"], Lp, w["M5"], b5, c5, 1, stream=stream, device=dev)
-            mobs[alpha].set_gauge(U)
-        return mobs[alpha]
+            mobs[(alpha, Lp)] = dwf.Lattice(w["dims"], Lp, w["M5"], b5, c5, 1, stream=stream, device=dev)
+            mobs[(alpha, Lp)].set_gauge(U)
+        return mobs[(alpha, Lp)]
+
+    if args.study_ls:
+        # Ls' and b + c (Sec. 4-5; Fig. 1 uses L' = 16 for L = 32), in the bench's solver settings
+        lat.cg(w["m"], b, tol=args.tol, inner="f32", delta=DELTA, check_every=CHECK_EVERY, out=x)  # warm-up
+        cases = []
+        for Lp in (8, 12, 16):
+            a0 = w["Ls"] / Lp
+            cases += [(Lp, a0, 1, 1e-3, 1e-2), (Lp, a0, 1, 1e-5, 1e-4), (Lp, a0, 2, 1e-5, 1e-4),
+                      (Lp, 0.75 * a0, 1, 1e-5, 1e-4), (Lp, 1.25 * a0, 1, 1e-5, 1e-4)]
+        for Lp, alpha, n_dc, tol_pv, tol_mob in cases:
+            e0, e1 = _events(2)
+            e0.record(stream)
+            r = dwf.madwf_solve(lat, mobius(alpha, Lp), w["m"], b, n_dc=n_dc, tol_pv=tol_pv, tol_mob=tol_mob,
+                                tol_final=args.tol, inner_prec="f32", delta=DELTA, check_every=CHECK_EVERY, out=x,
+                                max_iter=30000, raise_on_fail=False)
+            e1.record(stream)
+            e1.synchronize()
+            st = r.stats
+            print(json.dumps({"study": "madwf-Ls'", "Ls_inner": Lp, "b_plus_c": alpha, "n_dc": n_dc,
+                              "tol_pv": tol_pv, "tol_mob": tol_mob, "seconds": e0.elapsed_time(e1) / 1e3,
+                              "status": r.status,
+                              "op_count": {"pv": st["pv"]["op_count"], "mobius": st["mobius"]["op_count"],
+                                           "final": st["final_cg"]["op_count"], "total": st["total"]["op_count"]},
+                              "iters": {"pv": st["pv"]["iters"], "mobius": st["mobius"]["iters"],
+                                        "final": st["final_cg"]["iters"]},
+                              "pass_resid": st["pass_resid"], "true_resid": st["total"]["true_resid"]}), flush=True)
+            if len(mobs) > 2:  # keep device memory bounded: drop lattices not needed next
+                for key in [k for k in mobs if k[1] != Lp]:
+                    mobs.pop(key).close()
+        for mb in mobs.values():
+            mb.close()
+        lat.close()
+        return
+    Lp = w["inner_Ls"]
 
     base_alpha = w["Ls"] / Lp
     grid = [(w["eps"], 0, None, None, base_alpha)]

@@ -16,8 +16,8 @@ A step is one solve from a zero guess on seeded synthetic inputs already
 resident in HBM (timed with CUDA events on the solve's stream).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload madwf|mixed|hopprof|ladder]
-                  [--impl native|reference] [--study] [--md-study] [--hasenbusch-study] [--no-fp64]
-                  [--no-extras]
+                  [--impl native|reference] [--study [--study-ls]] [--md-study] [--hasenbusch-study]
+                  [--hmc-study] [--no-fp64] [--no-extras]
                   [--no-cpu-baseline]
 
 --study (with the madwf workload) sweeps the MADWF settings (defect-correction
@@ -127,6 +127,8 @@ def parse():
     ap.add_argument("--study", action="store_true", help="sweep the MADWF settings (madwf workload)")
     ap.add_argument("--study-ls", action="store_true", help="with --study: sweep Ls' and b + c in the bench's settings")
     ap.add_argument("--md-study", action="store_true", help="FGI against Omelyan trajectories on the force workload")
+    ap.add_argument("--hmc-study", action="store_true",
+                    help="HMC chains (heat bath, trajectory, Metropolis) with FGI and Omelyan on the force workload")
     ap.add_argument("--hasenbusch-study", action="store_true",
                     help="geometric and force-balanced Hasenbusch ladders, force solves at 1e-8 and 1e-6")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 CG comparison solve")
@@ -1003,6 +1005,48 @@ def run_hasenbusch_study(args, dev):
     lat.close()
 
 
+def run_hmc_study(args, dev):
+    """HMC chains (Sec. 2: heat bath, one trajectory, Metropolis) on the force
+    workload (Shamir 16^3 x 8 x Ls=16, terms (0.01, 0.1) and (0.1, 1),
+    eps = 0.5, seed 4): the force-gradient integrator at tau = 0.1 x 4 steps
+    against Omelyan 2MN at tau = 0.05 x 8 (about the same dH in the
+    trajectory study), 12 updates each from the same start and with the same
+    random numbers (update k uses seed 1000 + k).  One JSON line per chain:
+    acceptance, <dH>, <exp(-dH)> with its standard error, force evaluations
+    and time per update."""
+    import torch
+
+    from paper_1111_5059_gb300 import dwf, hmc, inputs
+
+    dims, Ls, M5 = (16, 16, 16, 8), 16, 1.8
+    terms = [(0.01, 0.1), (0.1, 1.0)]
+    stream = torch.cuda.current_stream(dev)
+    U0 = torch.from_numpy(inputs.gauge_field(4, dims, 0.5)).to(dev)
+    lat = dwf.Lattice(dims, Ls, M5, 1.0, 0.0, 1, stream=stream, device=dev)
+    for integ, tau, n in (("fgi", 0.1, 4), ("omelyan", 0.05, 8)):
+        U = U0.clone()
+        rows = []
+        e0, e1 = _events(2)
+        e0.record(stream)
+        for k in range(12):
+            rows.append(hmc.hmc_update(lat, U, terms, tau, n, 1000 + k, integrator=integ, tol=1e-10, inner="f32",
+                                       delta=DELTA))
+        e1.record(stream)
+        e1.synchronize()
+        dHs = [r["dH"] for r in rows]
+        w = [math.exp(-d) for d in dHs]
+        mean_w = sum(w) / len(w)
+        err_w = (sum((v - mean_w) ** 2 for v in w) / (len(w) - 1) / len(w)) ** 0.5
+        print(json.dumps({"study": "hmc", "workload": "force-shamir-16^3x8-Ls16-2terms", "integrator": integ,
+                          "tau": tau, "nsteps": n, "updates": len(rows),
+                          "acceptance": sum(r["accept"] for r in rows) / len(rows), "mean_dH": sum(dHs) / len(dHs),
+                          "mean_exp_minus_dH": mean_w, "stderr_exp_minus_dH": err_w, "dH": dHs,
+                          "force_evaluations_per_update": rows[0]["force_evaluations"],
+                          "cg_iters_per_update": sum(r["cg_iters"] for r in rows) / len(rows),
+                          "seconds_per_update": e0.elapsed_time(e1) / 1e3 / len(rows)}), flush=True)
+    lat.close()
+
+
 def main():
     args = parse()
     w = WORKLOADS[args.workload]
@@ -1027,6 +1071,9 @@ def main():
         return
     if args.hasenbusch_study:
         run_hasenbusch_study(args, dev)
+        return
+    if args.hmc_study:
+        run_hmc_study(args, dev)
         return
     if args.study:
         if not w["madwf"]:

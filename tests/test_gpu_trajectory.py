@@ -101,3 +101,35 @@ def test_force_workload_trajectories(dwf):
     ratio = abs(dH[("fgi", 0.2)]) / abs(dH[("fgi", 0.1)])
     assert 8.0 < ratio < 32.0, (dH, ratio)
     assert abs(dH[("fgi", 0.2)]) < abs(dH[("omelyan", 0.2)]), dH
+
+
+def test_hmc_chain_matches_oracle(small, dwf):
+    """Three HMC updates (heat bath, trajectory, Metropolis; Sec. 2) through
+    hmc.hmc_update on the GPU against the same chain with the oracle's heat
+    bath, trajectory, Hamiltonian and Metropolis rule, from the same random
+    numbers: the same decisions, dH and links.  A long step makes rejections
+    likely, so both branches are exercised."""
+    from paper_1111_5059_gb300 import hmc
+
+    lat, U, _, _ = small
+    dims, Ls = lat.dims, lat.Ls
+    Ut = _to(U)
+    Uo = U.copy()
+    decisions = []
+    for seed in (11, 12, 13, 14):
+        tau, n = 0.8, 1  # dH of 1.5-3: the chain accepts once and rejects three times
+        r = hmc.hmc_update(lat, Ut, TERMS, tau, n, seed, tol=1e-13, inner="f64", delta=0.1)
+        p, etas, u = hmc.draw(seed, dims, Ls, len(TERMS))
+        phis = [O.heatbath_phi(Uo, e, m1, m2, M5, tol=1e-14) for e, (m1, m2) in zip(etas, TERMS)]
+        H0 = O.hamiltonian(Uo, p, phis, TERMS, M5, tol=1e-14)
+        U1, p1, _ = O.md_trajectory(Uo, p, tau, n, phis, TERMS, M5, tol=1e-14)
+        dH = O.hamiltonian(U1, p1, phis, TERMS, M5, tol=1e-14) - H0
+        ok = O.metropolis_accept(dH, u)
+        assert r["accept"] == ok
+        assert abs(r["dH"] - dH) <= 1e-9 * abs(H0), (r["dH"], dH)
+        if ok:
+            Uo = U1
+        assert np.abs(Ut.cpu().numpy() - Uo).max() < 1e-10
+        decisions.append(ok)
+    lat.set_gauge(_to(U))
+    assert len(set(decisions)) == 2, decisions  # both an acceptance and a rejection

@@ -39,3 +39,43 @@ def test_reference_arm_json_line():
     assert abs(cb["algorithmic_gbs"] - 4 * (48 * 8 + 144 * 8 / 16) * sites / per_it / 1e9) < 1e-9 * cb["algorithmic_gbs"]
     assert abs(d["value"] - per_it * 250) < 1e-6 * d["value"]  # 250 FP64 CG iterations on this input
     assert d["e2e"] == {"value": d["value"], "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def _bench():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    return bench
+
+
+def test_traffic_figure_follows_the_measured_source_and_lh():
+    """roofline.traffic: algorithmic bytes times the ncu ratio at each
+    lattice's Lh, only for the kernel source the ratios were measured on."""
+    b = _bench()
+    ratios = b.HOP_TRAFFIC["ratio_by_lh"]
+    got = b.hop_traffic([(32, 1000.0), (12, 500.0)], 3)
+    if got is None:  # the kernel source changed since the capture
+        return
+    assert got == (1000.0 * ratios[16] + 500.0 * ratios[6]) / 3
+    assert b.hop_traffic([(10, 100.0)], 1) is None  # Lh = 5 was not measured
+    assert b.hop_traffic([(16, 100.0)], 0) is None
+
+
+def test_solver_settings_by_storage_precision():
+    b = _bench()
+    assert b.delta_for("f32") == b.DELTA and b.delta_for("f16") == b.DELTA_F16
+    assert 0 < b.DELTA < b.DELTA_F16 < 1 and b.CHECK_EVERY >= 1
+
+
+def test_huge_page_fraction_of_a_plain_buffer():
+    import mmap
+
+    import numpy as np
+    import torch
+
+    b = _bench()
+    m = mmap.mmap(-1, 1 << 22)
+    a = np.frombuffer(m, dtype=np.uint8)
+    a[:] = 1
+    f = b.thp_fraction(torch.from_numpy(a))
+    assert f is None or 0.0 <= f <= 1.0
